@@ -1,0 +1,207 @@
+/*
+ * proxsdp_gpu.h — C ABI of the GB300 (sm_103a) low-rank primal-dual SDP solver.
+ *
+ * The library implements the low-rank primal-dual hybrid gradient iteration
+ * "LR-PD-SDP" (Alg. 2 of Souto, Garcia & Veiga, "Exploiting Low-Rank
+ * Structure in Semidefinite Programming by Approximate Operator Splitting")
+ * and its full-projection special case "PD-SDP" (Alg. 1) for the general SDP
+ *
+ *     minimize tr(C X)  s.t.  tr(A_i X) = b_i (i < m_eq),
+ *                             tr(G_j X) <= h_j (the remaining rows),  X psd
+ *
+ * of Sec. 1.3 (Eq. sdp_general).  Every step of the iteration runs in the
+ * library's own CUDA kernels: the truncated psd projection of Sec. 3.1
+ * (Eq. trunc_eig) by a restarted block Lanczos solver, the rank update of
+ * Sec. 3.2, the rebuild X = V diag(max(lambda,0)) V^T fused with the primal
+ * update of Alg. 1 / Alg. 2, the sparse constraint operator M(X) and its
+ * adjoint M*(y), the dual step with the equality / inequality split of
+ * Sec. 2.3.1 (Eq. resolvent_1), and the residual / gap reductions of Sec. 2.2
+ * (Eq. comb_residual).  There is no CPU fallback: without a usable sm_103a
+ * device every entry point returns PROXSDP_ERR_CUDA.
+ *
+ * Conventions
+ * -----------
+ * - Symmetric matrices are passed as packed upper-triangle ("svec") entries
+ *   without sqrt(2) scaling: entry (i, j), 0 <= i <= j < n, has index
+ *   j*(j+1)/2 + i, and a value a there means A[i][j] = A[j][i] = a, so
+ *   tr(A X) = sum_i A_ii X_ii + 2 sum_{i<j} A_ij X_ij.
+ * - The constraint operator M = [A; G] (Sec. 2) is a CSR matrix whose row i
+ *   lists the svec entries of A_i (rows 0..m_eq-1) or G_{i-m_eq}.  A row whose
+ *   only entry has column index -1 is the structured dense matrix a * 11^T
+ *   (e.g. the equipartition constraint tr(11^T X) = 0 of Sec. 5.1).
+ * - The dual vector returned is the paper's y of the dual problem of Sec. 1.3
+ *   (maximise [b; h]^T y s.t. M*(y) <= C, y_ineq <= 0).  Internally the
+ *   iteration carries its negation (non-negative on inequality rows).
+ * - Every function returns an int status: 0 = OK, < 0 = error (codes below).
+ *   Non-convergence is not an error; it is reported in proxsdp_gpu_info.status.
+ *
+ * Ownership and threading
+ * -----------------------
+ * The caller owns every host array; set_problem copies what it needs.  A
+ * handle owns all device memory it allocates and frees it in destroy.  One
+ * handle is bound to one device and one CUDA stream and is not thread safe.
+ * Device-pointer entry points (proxsdp_gpu_aproj, _block_matvec, _sym_eig)
+ * read and write caller-owned device memory on the given stream and allocate
+ * their own scratch (released before they return).
+ */
+#ifndef PROXSDP_GPU_H
+#define PROXSDP_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define PROXSDP_OK 0
+#define PROXSDP_ERR_INVALID_ARG (-1) /* bad sizes, malformed CSR, NaN/Inf, NULL where required */
+#define PROXSDP_ERR_CUDA (-2)        /* CUDA runtime error, or no usable device */
+#define PROXSDP_ERR_OOM (-3)         /* device allocation failed */
+#define PROXSDP_ERR_BAD_STATE (-4)   /* e.g. solve before set_problem */
+#define PROXSDP_ERR_UNSUPPORTED (-5) /* size beyond a compiled limit */
+#define PROXSDP_ERR_TIMEOUT (-6)     /* a bounded device wait ran out */
+
+/* proxsdp_gpu_info.status */
+#define PROXSDP_CONVERGED 0           /* residuals and gap <= tol with a sufficient rank */
+#define PROXSDP_MAX_ITER 1            /* max_iter reached */
+#define PROXSDP_TIME_LIMIT 2          /* time_limit_s reached */
+#define PROXSDP_STALLED_AT_MAX_RANK 3 /* the rank rule asked for r > max_rank */
+#define PROXSDP_NUMERIC_ERROR 4       /* NaN/Inf in the iteration */
+
+/* precision of the S * V products and the rebuild */
+#define PROXSDP_PREC_FP32 0
+
+typedef struct proxsdp_gpu_ctx* proxsdp_gpu_t;
+
+/* Settings; proxsdp_gpu_settings_default fills the defaults listed here. */
+typedef struct {
+  double tol;             /* stop when max(rel_primal, rel_dual, rel_gap) <= tol      [1e-4] */
+  int64_t max_iter;       /* iteration cap                                              [1e6]  */
+  double time_limit_s;    /* wall-clock cap of one solve call (Sec. 5 uses 1200 s)      [1200] */
+  int full_eig;           /* 1: PD-SDP (Alg. 1, exact projection), 0: LR-PD-SDP (Alg. 2) [0]   */
+  int rank_init;          /* initial target rank r (Alg. 2 starts at 1)                  [8]   */
+  int block_size;         /* Lanczos block granularity b; block width = b*ceil((r+g)/b)  [16]  */
+  int window;             /* stall window l of Sec. 3.2 (<= 1024)                        [100] */
+  double eps_lambda;      /* rank test threshold of Alg. 2; <= 0 means tol               [0]   */
+  double alpha_frac;      /* step alpha = alpha_frac / ||M||_2 (Sec. 2.2: alpha<1/||M||) [0.95]*/
+  int precision;          /* PROXSDP_PREC_FP32                                           [0]   */
+  int normalize_rows;     /* scale each (A_i, rhs_i) to ||A_i||_F = 1                    [1]   */
+  uint64_t seed;          /* Lanczos start block                                         [1]   */
+  int max_rank;           /* cap on the target rank                                      [128] */
+  int lanczos_steps;      /* block Krylov steps per restart cycle (0: automatic)         [0]   */
+  int lanczos_max_cycles; /* restart cycles per projection                               [8]   */
+  double lanczos_tol;     /* Ritz residual tolerance relative to |theta_1| (0: adaptive) [0]   */
+  int guard;              /* extra Ritz vectors kept beyond r (0: automatic)             [0]   */
+  int check_every;        /* iterations between host checks of the stop status           [50]  */
+  int use_graphs;         /* run the iteration as a CUDA graph with conditional nodes    [1]   */
+} proxsdp_gpu_settings;
+
+typedef struct {
+  int status;                /* PROXSDP_CONVERGED, ... */
+  int final_rank;            /* target rank r at exit */
+  int64_t iters;             /* PDHG iterations */
+  int rank_changes;          /* number of rank doublings */
+  double primal_obj;         /* tr(C X) */
+  double dual_obj;           /* [b; h]^T y (paper's dual sign) */
+  double rel_primal_res;     /* eps_primal / (1 + ||C||_F) on the row-scaled problem */
+  double rel_dual_res;       /* eps_dual / (1 + ||rhs||_2) on the row-scaled problem */
+  double rel_gap;            /* |pobj - dobj| / (1 + |pobj| + |dobj|) */
+  double eps_primal;         /* Sec. 2.2 primal residual (row-scaled problem) */
+  double eps_dual;           /* Sec. 2.2 dual residual (row-scaled problem) */
+  double lambda_r;           /* r-th largest eigenvalue of the last projected matrix */
+  double solve_seconds;      /* device time of the solve call */
+  int64_t matvecs;           /* block products S * V (each reads S once) */
+  int64_t lanczos_cycles;    /* restart cycles over all projections */
+  int64_t lanczos_unconverged; /* projections that hit lanczos_max_cycles */
+  double alpha;              /* step size used */
+  double norm_M;             /* ||M||_2 of the row-scaled operator */
+} proxsdp_gpu_info;
+
+/* Fill *s with the defaults above. */
+int proxsdp_gpu_settings_default(proxsdp_gpu_settings* s);
+
+/* Create a solver bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL: the library creates its own).  `settings` may be NULL
+ * (defaults).  Returns PROXSDP_ERR_CUDA when the device is not usable. */
+int proxsdp_gpu_create(const proxsdp_gpu_settings* settings, int device, void* cuda_stream,
+                       proxsdp_gpu_t* out);
+
+/* Load a problem (Sec. 1.3).  C is dense (n*n doubles, symmetric; row and
+ * column major coincide) when C_dense != NULL, else sparse svec entries
+ * (c_nnz, c_idx, c_val; duplicates are summed).  A_rowptr has m_total+1
+ * entries, A_col/A_val A_rowptr[m_total] entries (svec indices, or a lone -1
+ * for a dense a*11^T row).  rhs = [b; h] (m_total).  Validates everything
+ * (sorted-or-not, in-range indices, finite values) and returns
+ * PROXSDP_ERR_INVALID_ARG on malformed input; copies the data to the device,
+ * scales rows (settings.normalize_rows) and computes ||M||_2 and alpha. */
+int proxsdp_gpu_set_problem(proxsdp_gpu_t h, int64_t n, const double* C_dense, int64_t c_nnz,
+                            const int64_t* c_idx, const double* c_val, int64_t m_total,
+                            int64_t m_eq, const int64_t* A_rowptr, const int64_t* A_col,
+                            const double* A_val, const double* rhs);
+
+/* Run Alg. 2 (or Alg. 1 with full_eig) from X = 0, y = 0 until convergence or a
+ * cap.  `info` may be NULL. */
+int proxsdp_gpu_solve(proxsdp_gpu_t h, proxsdp_gpu_info* info);
+
+/* Copy the last iterate to the host.  Any pointer may be NULL.
+ *   X      n*n doubles (dense V diag(max(lambda,0)) V^T),
+ *   y      m_total doubles, the paper's dual sign, original row scaling,
+ *   V      n*r doubles, column-major Ritz vectors (r = *r_out),
+ *   lambda r doubles, the Ritz values (unclamped),
+ *   r_out  the number of factors. */
+int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V,
+                                double* lambda, int64_t* r_out);
+
+/* Set the iterate (X = V diag(max(lambda,0)) V^T with V n*r column-major,
+ * orthonormal columns, and y in the paper's dual sign / original scaling) and
+ * the target rank, so that proxsdp_gpu_iterate continues from it.  Used for
+ * one-step parity against Alg. 1 / Alg. 2. */
+int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const double* lambda,
+                            const double* y);
+
+/* Run exactly `iters` iterations of Alg. 2 from the current iterate (rank
+ * rule active), then fill `info` with the residuals of the last one. */
+int proxsdp_gpu_iterate(proxsdp_gpu_t h, int64_t iters, proxsdp_gpu_info* info);
+
+/* Destroy the handle and free its device memory. */
+void proxsdp_gpu_destroy(proxsdp_gpu_t h);
+
+/* Last error message of the handle (or of the last failed create when h is
+ * NULL).  Valid until the next call on the handle. */
+const char* proxsdp_gpu_last_error(proxsdp_gpu_t h);
+
+/* ---------------------------------------------------------------------------
+ * Building blocks on caller-owned device memory (all pointers are device
+ * pointers; `cuda_stream` is a cudaStream_t or NULL for the legacy stream).
+ * ------------------------------------------------------------------------- */
+
+/* Truncated psd projection aproj(S, r) of Sec. 3.1 (Eq. trunc_eig):
+ * P = sum_{t<r} max(lambda_t, 0) v_t v_t^T over the r algebraically largest
+ * eigenpairs of the symmetric S (n x n FP32, row stride lds >= n).  Computed
+ * with the library's restarted block Lanczos (n > 128) or one-CTA Jacobi
+ * (n <= 128).  Outputs (each may be NULL): P (n x n FP32, stride ldp), V
+ * (n x r FP32 column-major, stride n), lambda (r FP64, descending,
+ * unclamped).  `settings` may be NULL.  `info` (may be NULL) receives
+ * matvecs / lanczos_cycles / lanczos_unconverged / lambda_r. */
+int proxsdp_gpu_aproj(const float* S, int64_t n, int64_t lds, int r, float* P, int64_t ldp,
+                      float* V, double* lambda, const proxsdp_gpu_settings* settings,
+                      void* cuda_stream, proxsdp_gpu_info* info);
+
+/* Symmetric block product W = S * Q (the Lanczos matvec): S n x n FP32 with
+ * row stride lds, Q n x k FP32 column-major (stride ldq >= n), W likewise
+ * (stride ldw).  k <= 256. */
+int proxsdp_gpu_block_matvec(const float* S, int64_t n, int64_t lds, const float* Q, int64_t ldq,
+                             int k, float* W, int64_t ldw, void* cuda_stream);
+
+/* Eigendecomposition of a small symmetric matrix T (K x K FP64 row-major,
+ * K <= 128) by cyclic Jacobi rotations in one thread block (the Rayleigh-Ritz
+ * step of the Lanczos solver): theta (K FP64, descending) and Y (K x K FP32
+ * column-major eigenvectors, column t for theta[t]). */
+int proxsdp_gpu_sym_eig(const double* T, int K, double* theta, float* Y, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PROXSDP_GPU_H */

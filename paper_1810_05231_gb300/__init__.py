@@ -1,0 +1,23 @@
+"""GB300 (sm_103a) low-rank primal-dual SDP solver (LR-PD-SDP, Alg. 2 of
+Souto, Garcia & Veiga) behind the C ABI of ``include/proxsdp_gpu.h``.
+
+The Python layer only marshals arguments to ``libproxsdp_gpu.so``; build the
+library with ``python -m paper_1810_05231_gb300.build``.
+"""
+from ._binding import (  # noqa: F401
+    CONVERGED,
+    MAX_ITER,
+    NUMERIC_ERROR,
+    STALLED_AT_MAX_RANK,
+    TIME_LIMIT,
+    EXPORTED,
+    Info,
+    ProxSDPError,
+    Settings,
+    Solver,
+    aproj,
+    block_matvec,
+    default_settings,
+    lib,
+    sym_eig,
+)

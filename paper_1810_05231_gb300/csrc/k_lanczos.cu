@@ -1,0 +1,521 @@
+// k_lanczos.cu — kernels of the restarted block Lanczos solver behind the
+// truncated psd projection aproj(S, r) of Sec. 3.1 (Eq. trunc_eig).
+//
+// The paper computes the r largest eigenpairs with a Krylov method (ARPACK on
+// a CPU, Sec. 3.1 / Sec. 4); here the Krylov basis lives in HBM as FP32
+// column blocks, inner products are accumulated exactly-rounded in a pair of
+// FP32 numbers (Knuth's TwoSum with the FMA-based TwoProduct of Ogita, Rump &
+// Oishi, "Accurate sum and dot product", 2005) and combined across blocks in
+// FP64, and the small Rayleigh-Ritz eigenproblem is solved by cyclic Jacobi
+// rotations in one thread block.
+#include "psdp.cuh"
+
+#include <math.h>
+
+namespace psdp {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+
+// Pseudo-random uniform in [-1, 1) from (seed, i, j): the splitmix64 finaliser
+// (Steele, Lea & Flood 2014) applied to a mixed counter.
+__device__ __forceinline__ float hash_uniform(unsigned long long seed, unsigned long long i,
+                                              unsigned long long j) {
+  unsigned long long x = seed + 0x9E3779B97F4A7C15ULL * (i + 1) + 0xC2B2AE3D27D4EB4FULL * (j + 7);
+  x ^= x >> 30;
+  x *= 0xBF58476D1CE4E5B9ULL;
+  x ^= x >> 27;
+  x *= 0x94D049BB133111EBULL;
+  x ^= x >> 31;
+  return (float)(x >> 40) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+// Accumulator of a sum of exact FP32 products in two FP32 words.
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() : hi(0.f), lo(0.f) {}
+  // s += a * b : the product is split exactly (p + e = a*b) with one FMA and
+  // p is added to hi with TwoSum; the rounding errors go to lo.
+  __device__ __forceinline__ void fma_acc(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = fmaf(a, b, -p);
+    float s = __fadd_rn(hi, p);
+    float bb = __fsub_rn(s, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// ---------------------------------------------------------------------------
+// S * Q block product (SIMT version)
+// ---------------------------------------------------------------------------
+// CTA tile: 32 rows of S x 16 columns of Q, K-chunks of 64.  S symmetric, so
+// row blocks of S are also column blocks.
+constexpr int MV_RB = 32, MV_CB = 16, MV_KC = 64;
+
+__global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ S, int lds, int n,
+                                                      const float* __restrict__ Q, int ldq,
+                                                      float* __restrict__ W, int ldw, int k,
+                                                      const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ float Ss[MV_RB][MV_KC + 1];
+  __shared__ float Qs[MV_KC][MV_CB + 1];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * MV_RB;
+  const int c0 = blockIdx.y * MV_CB;
+  const int tx = tid % MV_CB, ty = tid / MV_CB;  // ty in [0,16)
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int k0 = 0; k0 < n; k0 += MV_KC) {
+    for (int idx = tid; idx < MV_RB * MV_KC; idx += 256) {
+      int rr = idx / MV_KC, kk = idx % MV_KC;
+      int gr = r0 + rr, gk = k0 + kk;
+      Ss[rr][kk] = (gr < n && gk < n) ? S[(size_t)gr * lds + gk] : 0.f;
+    }
+    for (int idx = tid; idx < MV_KC * MV_CB; idx += 256) {
+      int cc = idx / MV_KC, kk = idx % MV_KC;
+      int gc = c0 + cc, gk = k0 + kk;
+      Qs[kk][cc] = (gc < k && gk < n) ? Q[(size_t)gc * ldq + gk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 16
+    for (int kk = 0; kk < MV_KC; ++kk) {
+      float q = Qs[kk][tx];
+      acc0 = fmaf(Ss[ty][kk], q, acc0);
+      acc1 = fmaf(Ss[ty + 16][kk], q, acc1);
+    }
+    __syncthreads();
+  }
+  int gc = c0 + tx;
+  if (gc < k) {
+    if (r0 + ty < n) W[(size_t)gc * ldw + r0 + ty] = acc0;
+    if (r0 + ty + 16 < n) W[(size_t)gc * ldw + r0 + ty + 16] = acc1;
+  }
+}
+
+void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
+                         int k, const int* skip, cudaStream_t st) {
+  dim3 grid((n + MV_RB - 1) / MV_RB, (k + MV_CB - 1) / MV_CB);
+  k_block_matvec<<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, skip);
+}
+
+// ---------------------------------------------------------------------------
+// random start block
+// ---------------------------------------------------------------------------
+__global__ void k_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t total = (size_t)n * k;
+  if (idx >= total) return;
+  int c = (int)(idx / n), i = (int)(idx % n);
+  Q[(size_t)(col0 + c) * ldq + i] = hash_uniform(seed, (unsigned long long)i, (unsigned long long)(col0 + c));
+}
+
+void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
+                         cudaStream_t st) {
+  size_t total = (size_t)n * k;
+  int blocks = (int)((total + 255) / 256);
+  k_random_block<<<blocks, 256, 0, st>>>(Q, ldq, n, col0, k, seed);
+}
+
+// ---------------------------------------------------------------------------
+// Gram H = A^T B with exact-product accumulation
+// ---------------------------------------------------------------------------
+// Grid (tiles_a * tiles_b, nsplit).  Each CTA computes a 16 x 16 output tile
+// over one row range; the last CTA of each output tile adds the nsplit
+// partials in fixed order (deterministic).
+constexpr int GR_T = 16, GR_RC = 64;
+
+__global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int lda, int ka,
+                                              const float* __restrict__ B, int ldb, int kb, int n,
+                                              int rows_per_split, double* __restrict__ H,
+                                              double* __restrict__ part, unsigned* counters,
+                                              const int* skip, int act, int slot) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ float As[GR_RC][GR_T + 1];
+  __shared__ float Bs[GR_RC][GR_T + 1];
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x;
+  int a0, b0;
+  if (act > 0) {
+    // only the first `act` columns of every `slot`-wide column group
+    const int per = (act + GR_T - 1) / GR_T;
+    const int tiles_b = per * (kb / slot);
+    const int ta = blockIdx.x / tiles_b, tb = blockIdx.x % tiles_b;
+    a0 = (ta / per) * slot + (ta % per) * GR_T;
+    b0 = (tb / per) * slot + (tb % per) * GR_T;
+  } else {
+    const int tiles_b = (kb + GR_T - 1) / GR_T;
+    a0 = (blockIdx.x / tiles_b) * GR_T;
+    b0 = (blockIdx.x % tiles_b) * GR_T;
+  }
+  const int ty = tid / GR_T, tx = tid % GR_T;
+  const int rbeg = blockIdx.y * rows_per_split;
+  const int rend = min(n, rbeg + rows_per_split);
+  DF acc;
+  for (int i0 = rbeg; i0 < rend; i0 += GR_RC) {
+    for (int idx = tid; idx < GR_RC * GR_T; idx += 256) {
+      int c = idx / GR_RC, i = idx % GR_RC;
+      int gi = i0 + i;
+      As[i][c] = (gi < rend && a0 + c < ka) ? A[(size_t)(a0 + c) * lda + gi] : 0.f;
+      Bs[i][c] = (gi < rend && b0 + c < kb) ? B[(size_t)(b0 + c) * ldb + gi] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int i = 0; i < GR_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
+    __syncthreads();
+  }
+  // partials of this output tile: part[(tile * nsplit + split) * 256 + local]
+  double* my = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (GR_T * GR_T);
+  my[tid] = acc.value();
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    unsigned prev = atomicAdd(&counters[blockIdx.x], 1u);
+    s_last = (prev == gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int a = a0 + ty, b = b0 + tx;
+  if (a < ka && b < kb) {
+    double s = 0.0;
+    const double* base = part + (size_t)blockIdx.x * gridDim.y * (GR_T * GR_T);
+    for (int sp = 0; sp < (int)gridDim.y; ++sp) s += __ldcg(&base[(size_t)sp * (GR_T * GR_T) + tid]);
+    H[(size_t)a * kb + b] = s;
+  }
+  if (tid == 0) counters[blockIdx.x] = 0u;
+}
+
+void launch_gram(const float* A, int lda, int ka, const float* B, int ldb, int kb, int n, double* H,
+                 double* part, unsigned* counter, const int* skip, cudaStream_t st, int act,
+                 int slot) {
+  int tiles = ((ka + GR_T - 1) / GR_T) * ((kb + GR_T - 1) / GR_T);
+  if (act > 0) {
+    int per = (act + GR_T - 1) / GR_T;
+    tiles = per * (ka / slot) * per * (kb / slot);
+  }
+  int nsplit = 148 / tiles;
+  if (nsplit < 1) nsplit = 1;
+  int rows = (n + nsplit - 1) / nsplit;
+  if (rows < 128) rows = 128;
+  nsplit = (n + rows - 1) / rows;
+  if (nsplit < 1) nsplit = 1;
+  dim3 grid(tiles, nsplit);
+  k_gram<<<grid, 256, 0, st>>>(A, lda, ka, B, ldb, kb, n, rows, H, part, counter, skip, act,
+                               slot > 0 ? slot : 1);
+}
+
+// ---------------------------------------------------------------------------
+// Z -= A * H  (classical Gram-Schmidt update)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_block_update(float* __restrict__ Z, int ldz, int kb,
+                                                      const float* __restrict__ A, int lda, int ka,
+                                                      const double* __restrict__ H, int n,
+                                                      const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ float Hs[];  // ka x kb
+  for (int idx = threadIdx.x; idx < ka * kb; idx += blockDim.x) Hs[idx] = (float)H[idx];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= n) return;
+  float acc = 0.f;
+  for (int a = 0; a < ka; ++a) acc = fmaf(A[(size_t)a * lda + i], Hs[a * kb + b], acc);
+  Z[(size_t)b * ldz + i] -= acc;
+}
+
+void launch_block_update(float* Z, int ldz, int kb, const float* A, int lda, int ka, const double* H,
+                         int n, const int* skip, cudaStream_t st) {
+  if (ka == 0) return;
+  dim3 grid((n + 255) / 256, kb);
+  k_block_update<<<grid, 256, (size_t)ka * kb * sizeof(float), st>>>(Z, ldz, kb, A, lda, ka, H, n, skip);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of the w x w Gram (FP64, one CTA) with deficient-column detection
+// ---------------------------------------------------------------------------
+// Writes the upper factor R (G = R^T R) as FP32 into Rout (w x w row-major,
+// diagonal stored as 1/R_jj) and flags[j] = 1 for columns whose remaining
+// norm fell below 1e-10 of their original norm (numerically dependent).
+__global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int w,
+                                              float* __restrict__ Rout, int* __restrict__ flags,
+                                              const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ double Gs[kMaxW][kMaxW + 1];
+  __shared__ double d0[kMaxW];
+  __shared__ int fl[kMaxW];
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int i = idx / w, j = idx % w;
+    Gs[i][j] = 0.5 * (G[i * w + j] + G[j * w + i]);
+  }
+  __syncthreads();
+  for (int j = tid; j < w; j += blockDim.x) {
+    d0[j] = Gs[j][j];
+    fl[j] = 0;
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      double piv = Gs[j][j];
+      if (!(piv > 1e-10 * d0[j]) || !(d0[j] > 0.0)) {
+        fl[j] = 1;
+        Gs[j][j] = 1.0;
+      } else {
+        Gs[j][j] = sqrt(piv);
+      }
+    }
+    __syncthreads();
+    const double djj = Gs[j][j];
+    const int def = fl[j];
+    for (int l = j + 1 + tid; l < w; l += blockDim.x) Gs[j][l] = def ? 0.0 : Gs[j][l] / djj;
+    __syncthreads();
+    const int rem = w - j - 1;
+    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+      int k = j + 1 + idx / rem, l = j + 1 + idx % rem;
+      if (l >= k) Gs[k][l] -= Gs[j][k] * Gs[j][l];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int i = idx / w, j = idx % w;
+    float v = 0.f;
+    if (i == j) v = (float)(1.0 / Gs[i][i]);
+    else if (j > i) v = (float)Gs[i][j];
+    Rout[idx] = v;
+  }
+  for (int j = tid; j < w; j += blockDim.x) flags[j] = fl[j];
+}
+
+void launch_chol_inv(const double* G, int w, float* Rinv, int* flags, const int* skip, cudaStream_t st) {
+  k_chol<<<1, 256, 0, st>>>(G, w, Rinv, flags, skip);
+}
+
+// Z <- Z R^{-1} by forward substitution on each row (x R = z); flagged columns
+// are replaced by pseudo-random entries (re-orthogonalised by the caller).
+__global__ void __launch_bounds__(128) k_apply_rinv(float* __restrict__ Z, int ldz, int w,
+                                                    const float* __restrict__ R, const int* flags,
+                                                    int n, unsigned long long seed, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  __shared__ float Rs[kMaxW * kMaxW];
+  __shared__ int fl[kMaxW];
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) Rs[idx] = R[idx];
+  for (int j = threadIdx.x; j < w; j += blockDim.x) fl[j] = flags[j];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x[kMaxW];
+#pragma unroll
+  for (int j = 0; j < kMaxW; ++j) {
+    if (j < w) {
+      float z = Z[(size_t)j * ldz + i];
+      for (int k = 0; k < j; ++k) z = fmaf(-x[k], Rs[k * w + j], z);
+      x[j] = fl[j] ? hash_uniform(seed, (unsigned long long)i, (unsigned long long)(1000 + j))
+                   : z * Rs[j * w + j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxW; ++j)
+    if (j < w) Z[(size_t)j * ldz + i] = x[j];
+}
+
+void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* flags, int n,
+                       unsigned long long seed, const int* skip, cudaStream_t st) {
+  k_apply_rinv<<<(n + 127) / 128, 128, 0, st>>>(Z, ldz, w, Rinv, flags, n, seed, skip);
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric eigensolver: parallel cyclic Jacobi in one CTA
+// ---------------------------------------------------------------------------
+// Round-robin ordering: in round s (0..K-2) position K-1 meets s and, for
+// t = 1..K/2-1, (s+t) mod (K-1) meets (s-t) mod (K-1); every pair meets once
+// per sweep and the K/2 rotations of a round act on disjoint index pairs.
+// Each rotation J (c, s in the (p,q) plane) is chosen to zero A_pq
+// (tan 2 theta = 2 A_pq / (A_qq - A_pp)); A <- J^T A J, V <- V J.
+template <typename T>
+struct JacobiTraits;
+template <>
+struct JacobiTraits<float> {
+  static constexpr double tol2 = 1e-14;
+};
+template <>
+struct JacobiTraits<double> {
+  static constexpr double tol2 = 1e-28;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, int K, int Kp,
+                                                double* __restrict__ theta, T* __restrict__ Yout,
+                                                int ldy, int nout, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  extern __shared__ unsigned char smraw[];
+  const int ld = Kp + 1;
+  T* A = reinterpret_cast<T*>(smraw);
+  T* V = A + (size_t)Kp * ld;
+  T* cs = V + (size_t)Kp * ld;      // Kp/2 cosines
+  T* sn = cs + Kp / 2;              // Kp/2 sines
+  int* pp = reinterpret_cast<int*>(sn + Kp / 2);
+  int* qq = pp + Kp / 2;
+  double* red = reinterpret_cast<double*>(qq + Kp / 2 + 2);  // 2 * 32 doubles (8-aligned below)
+  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int half = Kp / 2;
+
+  // load (symmetrised); padded indices get an isolated, very negative diagonal
+  double dmin = 0.0;
+  for (int idx = tid; idx < Kp * Kp; idx += nth) {
+    int i = idx / Kp, j = idx % Kp;
+    double v = 0.0;
+    if (i < K && j < K) v = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
+    A[i * ld + j] = (T)v;
+    V[i * ld + j] = (T)(i == j ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (Kp > K) {
+    if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < K; ++i) s += fabs((double)A[i * ld + i]);
+      for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) s = fmax(s, fabs((double)A[i * ld + j]));
+      dmin = -4.0 * (s + 1.0) * K;
+      for (int i = K; i < Kp; ++i) A[i * ld + i] = (T)dmin;
+    }
+    __syncthreads();
+  }
+
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    // convergence test: off(A)^2 <= tol2 * ||A||_F^2
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < K * K; idx += nth) {
+      int i = idx / K, j = idx % K;
+      double v = (double)A[i * ld + j];
+      tot += v * v;
+      if (i != j) off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if ((tid & 31) == 0) {
+      red[tid >> 5] = off;
+      red[32 + (tid >> 5)] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double o2 = 0.0, t2 = 0.0;
+      for (int k = 0; k < (nth >> 5); ++k) {
+        o2 += red[k];
+        t2 += red[32 + k];
+      }
+      s_stop = (o2 <= JacobiTraits<T>::tol2 * t2) || (t2 == 0.0);
+    }
+    __syncthreads();
+    if (s_stop) break;
+    for (int round = 0; round < Kp - 1; ++round) {
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = round;
+          q = Kp - 1;
+        } else {
+          p = (round + tid) % (Kp - 1);
+          q = (round - tid + (Kp - 1)) % (Kp - 1);
+        }
+        if (p > q) {
+          int t = p;
+          p = q;
+          q = t;
+        }
+        T apq = A[p * ld + q];
+        T c = (T)1, s = (T)0;
+        if (apq != (T)0) {
+          T app = A[p * ld + p], aqq = A[q * ld + q];
+          T tau = (aqq - app) / ((T)2 * apq);
+          T t;
+          if (fabs((double)tau) > 1e15) t = (T)0.5 / tau;
+          else t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+          c = (T)1 / sqrt((T)1 + t * t);
+          s = t * c;
+        }
+        cs[tid] = c;
+        sn[tid] = s;
+        pp[tid] = p;
+        qq[tid] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = tid; idx < half * Kp; idx += nth) {
+        int t = idx / Kp, j = idx % Kp;
+        int p = pp[t], q = qq[t];
+        T c = cs[t], s = sn[t];
+        T ap = A[p * ld + j], aq = A[q * ld + j];
+        A[p * ld + j] = c * ap - s * aq;
+        A[q * ld + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = tid; idx < half * Kp; idx += nth) {
+        int t = idx / Kp, i = idx % Kp;
+        int p = pp[t], q = qq[t];
+        T c = cs[t], s = sn[t];
+        T ap = A[i * ld + p], aq = A[i * ld + q];
+        A[i * ld + p] = c * ap - s * aq;
+        A[i * ld + q] = s * ap + c * aq;
+        T vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - s * vq;
+        V[i * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      if (tid < half) {  // the rotation annihilates A_pq exactly
+        A[pp[tid] * ld + qq[tid]] = (T)0;
+        A[qq[tid] * ld + pp[tid]] = (T)0;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues descending (rank by comparison, ties by index)
+  for (int i = tid; i < K; i += nth) {
+    double di = (double)A[i * ld + i];
+    int rank = 0;
+    for (int j = 0; j < K; ++j) {
+      double dj = (double)A[j * ld + j];
+      rank += (dj > di) || (dj == di && j < i);
+    }
+    if (rank < nout) {
+      theta[rank] = di;
+      for (int row = 0; row < K; ++row) Yout[(size_t)rank * ldy + row] = V[row * ld + i];
+    }
+  }
+}
+
+template <typename T>
+static size_t jacobi_smem(int Kp) {
+  size_t ld = Kp + 1;
+  return (2 * (size_t)Kp * ld + (size_t)Kp) * sizeof(T) + ((size_t)Kp + 2) * sizeof(int) + 8 +
+         64 * sizeof(double);
+}
+
+void init_lanczos_attributes() {
+  cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)jacobi_smem<float>(kMaxK));
+  cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)jacobi_smem<double>(kFullEigMax - 24));
+}
+
+void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
+                    const int* skip, cudaStream_t st) {
+  int Kp = (K + 1) & ~1;
+  size_t sm = jacobi_smem<float>(Kp);
+  k_jacobi<float><<<1, 512, sm, st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
+}
+
+void launch_sym_eig_f64(const double* T, int K, double* theta, double* Y, int ldy, cudaStream_t st) {
+  int Kp = (K + 1) & ~1;
+  size_t sm = jacobi_smem<double>(Kp);
+  k_jacobi<double><<<1, 512, sm, st>>>(T, K, Kp, theta, Y, ldy, K, nullptr);
+}
+
+}  // namespace psdp

@@ -1,0 +1,618 @@
+// k_pdhg.cu — the primal-dual part of one LR-PD-SDP iteration (Alg. 2):
+// Ritz-vector assembly and the projection's convergence test, the constraint
+// operator M(X) evaluated from the factors of X, the dual step with the
+// equality / inequality split (Sec. 2.3.1, Eq. resolvent_1), the adjoint
+// D = C + M*(y), the residuals of Sec. 2.2 (Eq. comb_residual), the rank
+// rule of Sec. 3.2, and the rebuild of the next primal-step input
+// S = V diag(max(lambda,0)) V^T - alpha (C + M*(y)) (Alg. 2 primal step).
+#include "psdp.cuh"
+
+#include <math.h>
+
+namespace psdp {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of `nv` doubles per thread into out[0..nv) (thread 0 holds
+// the result).  `sh` needs 32 * nv doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int q = 0; q < nw; ++q) s += sh[k * 32 + q];
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Returns true in every thread of the last block to arrive (after all blocks
+// stored their partials and fenced).
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ unsigned s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Ritz vectors V = Q Y, S V = W Y, residuals and the projection's stop test
+// ---------------------------------------------------------------------------
+constexpr int RZ_RB = 32;
+
+__global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, int r, int s_steps,
+                                              cudaGraphConditionalHandle cond, int use_cond) {
+  Ctl* ctl = wk.ctl;
+  if (*(volatile int*)&ctl->lz_done) return;
+  extern __shared__ float sm[];
+  const int ldk = K + 1;
+  float* Qs = sm;                      // RB x (K+1)
+  float* Ws = Qs + RZ_RB * ldk;        // RB x (K+1)
+  float* Ys = Ws + RZ_RB * ldk;        // K x w
+  float* Vs = Ys + K * w;              // RB x (w+1)
+  float* WVs = Vs + RZ_RB * (w + 1);   // RB x (w+1)
+  __shared__ double th[kMaxW];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * RZ_RB;
+  const int rows = min(RZ_RB, n - r0);
+  const int nw = 1 - ctl->par;  // buffer of the new iterate
+  for (int idx = tid; idx < RZ_RB * K; idx += blockDim.x) {
+    int k = idx / RZ_RB, i = idx % RZ_RB;
+    float q = 0.f, ww = 0.f;
+    if (i < rows) {
+      q = wk.Q[(size_t)k * wk.ldq + r0 + i];
+      ww = wk.W[(size_t)k * wk.ldq + r0 + i];
+    }
+    Qs[i * ldk + k] = q;
+    Ws[i * ldk + k] = ww;
+  }
+  for (int idx = tid; idx < K * w; idx += blockDim.x) {
+    int t = idx / K, k = idx % K;
+    Ys[k * w + t] = wk.Y[(size_t)t * kMaxK + k];
+  }
+  for (int t = tid; t < w; t += blockDim.x) th[t] = wk.theta[t];
+  __syncthreads();
+  for (int o = tid; o < RZ_RB * w; o += blockDim.x) {
+    int i = o / w, t = o % w;
+    float v = 0.f, u = 0.f;
+    for (int k = 0; k < K; ++k) {
+      float y = Ys[k * w + t];
+      v = fmaf(Qs[i * ldk + k], y, v);
+      u = fmaf(Ws[i * ldk + k], y, u);
+    }
+    Vs[i * (w + 1) + t] = v;
+    WVs[i * (w + 1) + t] = u;
+  }
+  __syncthreads();
+  // in-place write-back (each CTA owns its rows), row-major copy of V
+  for (int o = tid; o < RZ_RB * w; o += blockDim.x) {
+    int t = o / RZ_RB, i = o % RZ_RB;
+    if (i < rows) {
+      wk.Q[(size_t)t * wk.ldq + r0 + i] = Vs[i * (w + 1) + t];
+      wk.W[(size_t)t * wk.ldq + r0 + i] = WVs[i * (w + 1) + t];
+    }
+  }
+  for (int o = tid; o < RZ_RB * w; o += blockDim.x) {
+    int i = o / w, t = o % w;
+    if (i < rows) wk.Vrm[nw][(size_t)(r0 + i) * wk.ldv + t] = Vs[i * (w + 1) + t];
+  }
+  // partial sums per Ritz column: ||wv - theta v||^2, v.wv, v.v, sum v
+  double* part = wk.ritz_part + (size_t)blockIdx.x * 4 * kMaxW;
+  for (int t = tid; t < w; t += blockDim.x) {
+    double a = 0, b = 0, c = 0, d = 0;
+    float tht = (float)th[t];
+    for (int i = 0; i < rows; ++i) {
+      float v = Vs[i * (w + 1) + t], u = WVs[i * (w + 1) + t];
+      float res = fmaf(-tht, v, u);
+      a += (double)res * res;
+      b += (double)v * u;
+      c += (double)v * v;
+      d += (double)v;
+    }
+    part[t] = a;
+    part[kMaxW + t] = b;
+    part[2 * kMaxW + t] = c;
+    part[3 * kMaxW + t] = d;
+  }
+  if (!last_block(&wk.counters[CNT_RITZ * 512])) return;
+  // final reduction in block order
+  __shared__ double fin[4 * kMaxW];
+  for (int t = tid; t < w; t += blockDim.x) {
+    double a = 0, b = 0, c = 0, d = 0;
+    for (int bk = 0; bk < (int)gridDim.x; ++bk) {
+      const double* p = wk.ritz_part + (size_t)bk * 4 * kMaxW;
+      a += __ldcg(&p[t]);
+      b += __ldcg(&p[kMaxW + t]);
+      c += __ldcg(&p[2 * kMaxW + t]);
+      d += __ldcg(&p[3 * kMaxW + t]);
+    }
+    fin[t] = a;
+    fin[kMaxW + t] = b;
+    fin[2 * kMaxW + t] = c;
+    fin[3 * kMaxW + t] = d;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double scale = 0.0;
+    for (int t = 0; t < w; ++t) scale = fmax(scale, fabs(th[t]));
+    if (scale == 0.0) scale = 1.0;
+    double worst = 0.0;
+    for (int t = 0; t < w; ++t) {
+      double vv = fin[2 * kMaxW + t];
+      double lam = vv > 0.0 ? fin[kMaxW + t] / vv : th[t];  // Rayleigh quotient (FP64 sums)
+      wk.lam[nw][t] = lam;
+      wk.colsum[nw][t] = fin[3 * kMaxW + t];
+      double res = sqrt(fin[t] / (vv > 0.0 ? vv : 1.0));
+      if (t < r) worst = fmax(worst, res / scale);
+    }
+    for (int t = w; t < wk.ldv; ++t) {
+      wk.lam[nw][t] = 0.0;
+      wk.colsum[nw][t] = 0.0;
+    }
+    ctl->lz_res = worst;
+    ctl->lz_cycle += 1;
+    ctl->lz_cycles_total += 1;
+    ctl->matvecs += s_steps;
+    bool ok = worst <= ctl->lz_tol || !(worst == worst);
+    if (ok || ctl->lz_cycle >= ctl->max_cycles) {
+      if (!ok) ctl->lz_unconverged += 1;
+      ctl->lz_done = 1;
+    }
+    if (use_cond) cudaGraphSetConditional(cond, ctl->lz_done ? 0u : 1u);
+    wk.counters[CNT_RITZ * 512] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// M_ext(X) chunk partials: X = sum_{t<r} max(lambda_t,0) v_t v_t^T
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mx(DevProblem pb, DevWork wk, int r) {
+  __shared__ float lp[kMaxR];
+  const int nw = 1 - wk.ctl->par;
+  for (int t = threadIdx.x; t < kMaxR; t += blockDim.x) lp[t] = (t < r) ? (float)fmax(wk.lam[nw][t], 0.0) : 0.f;
+  __syncthreads();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= pb.n_chunks) return;
+  const float* V = wk.Vrm[nw];
+  double acc = 0.0;
+  for (int e = pb.chunk_beg[warp] + lane; e < pb.chunk_end[warp]; e += 32) {
+    const float* vp = V + (size_t)pb.ent_p[e] * wk.ldv;
+    const float* vq = V + (size_t)pb.ent_q[e] * wk.ldv;
+    float x = 0.f;
+#pragma unroll 8
+    for (int t = 0; t < r; ++t) x = fmaf(lp[t] * vp[t], vq[t], x);
+    acc += pb.ent_a[e] * (double)x;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) wk.chunk_part[warp] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// dual step (Alg. 2 dual parts 1 and 2) and its reductions
+// ---------------------------------------------------------------------------
+// y_half = y + alpha (2 M(X+) - M(X)); equality rows y+ = y_half - alpha b,
+// inequality rows y+ = max(y_half - alpha h, 0)  (= y_half - alpha proj(y_half/alpha)).
+__global__ void __launch_bounds__(256) k_dual(DevProblem pb, DevWork wk, int r) {
+  __shared__ double sh[32 * 4];
+  Ctl* ctl = wk.ctl;
+  const int nw = 1 - ctl->par, od = ctl->par;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const double alpha = pb.alpha;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < pb.m) {
+    double mxn = 0.0;
+    for (int c = pb.row_chunk[i]; c < pb.row_chunk[i + 1]; ++c) mxn += wk.chunk_part[c];
+    if (pb.n_dense) {
+      const int d = pb.dense_of_row[i];
+      if (d >= 0) {  // tr(a 11^T X) = a sum_t max(lambda_t,0) (1^T v_t)^2
+        double s = 0.0;
+        for (int t = 0; t < r; ++t) {
+          double cs = wk.colsum[nw][t];
+          s += fmax(wk.lam[nw][t], 0.0) * cs * cs;
+        }
+        mxn += pb.dense_a[d] * s;
+      }
+    }
+    const double mxo = wk.mx[od][i];
+    const double yo = wk.y[i];
+    const double yh = yo + alpha * (2.0 * mxn - mxo);
+    const double yn = (i < pb.m_eq) ? yh - alpha * pb.rhs[i] : fmax(yh - alpha * pb.rhs[i], 0.0);
+    const double dyv = yn - yo;
+    wk.y[i] = yn;
+    wk.dy[i] = dyv;
+    wk.mx[nw][i] = mxn;
+    const double dmx = mxn - mxo;
+    const double ed = dyv / alpha - dmx;
+    v[0] = ed * ed;           // eps_dual^2
+    v[1] = dyv * dmx;         // <dy, M(dX)> = <M*(dy), dX>
+    v[2] = pb.rhs[i] * yn;    // rhs^T y
+  }
+  block_sum<4>(v, sh);
+  double* part = wk.part + (size_t)blockIdx.x * 4;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) part[k] = v[k];
+  if (!last_block(&wk.counters[CNT_DUAL * 512])) return;
+  if (threadIdx.x == 0) {
+    double s[4] = {0, 0, 0, 0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+      for (int k = 0; k < 4; ++k) s[k] += __ldcg(&wk.part[(size_t)b * 4 + k]);
+    // objective row m: tr(C X+)
+    double pobj = 0.0;
+    for (int c = pb.row_chunk[pb.m]; c < pb.row_chunk[pb.m + 1]; ++c) pobj += __ldcg(&wk.chunk_part[c]);
+    wk.mx[nw][pb.m] = pobj;
+    ctl->red_dual[0] = s[0];
+    ctl->red_dual[1] = s[1];
+    ctl->red_dual[2] = s[2];
+    ctl->red_dual[3] = pobj;
+    wk.counters[CNT_DUAL * 512] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// D = C + M*(y) on the union pattern, and ||M*(dy)||_F^2
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dvals(DevProblem pb, DevWork wk) {
+  __shared__ double sh[32 * 2];
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (u < pb.nU) {
+    double d = pb.u_c[u], md = 0.0;
+    for (int j = pb.u_ptr[u]; j < pb.u_ptr[u + 1]; ++j) {
+      d += wk.y[pb.u_row[j]] * pb.u_a[j];
+      md += wk.dy[pb.u_row[j]] * pb.u_a[j];
+    }
+    wk.D[u] = d;
+    const double wgt = (pb.u_p[u] == pb.u_q[u]) ? 1.0 : 2.0;
+    v[0] = wgt * md * md;
+    v[1] = wgt * md;
+  }
+  block_sum<2>(v, sh);
+  double* part = wk.part + (size_t)blockIdx.x * 2;
+  if (threadIdx.x == 0) {
+    part[0] = v[0];
+    part[1] = v[1];
+  }
+  if (!last_block(&wk.counters[CNT_DVALS * 512])) return;
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      s0 += __ldcg(&wk.part[(size_t)b * 2]);
+      s1 += __ldcg(&wk.part[(size_t)b * 2 + 1]);
+    }
+    double sh0 = 0.0, sh1 = 0.0;
+    for (int d = 0; d < pb.n_dense; ++d) {
+      sh0 += pb.dense_a[d] * wk.y[pb.dense_row[d]];
+      sh1 += pb.dense_a[d] * wk.dy[pb.dense_row[d]];
+    }
+    wk.dshift[0] = sh0;
+    wk.dshift[1] = sh1;
+    // ||sparse + sh1 11^T||_F^2
+    wk.ctl->red_dvals[0] = s0 + 2.0 * sh1 * s1 + sh1 * sh1 * (double)pb.n * (double)pb.n;
+    wk.counters[CNT_DVALS * 512] = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// controller: residuals (Sec. 2.2), stop test, rank rule (Sec. 3.2)
+// ---------------------------------------------------------------------------
+// G is the Gram of the column-major factor slots [slot0 | slot1] (2*kMaxR
+// columns); X = V_s Lambda_+ V_s^T for slot s, so
+// ||X1 - X0||_F^2 = sum lam1 lam1 G11^2 + sum lam0 lam0 G00^2 - 2 sum lam1 lam0 G10^2.
+__global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, const double* G,
+                                                 cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double sh[32 * 3];
+  Ctl* ctl = wk.ctl;
+  const int nw = 1 - ctl->par, od = ctl->par;
+  const int r = ctl->r, ro = ctl->r_old;
+  const int ldg = 2 * kMaxR;
+  const int on = nw * kMaxR, oo = od * kMaxR;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int idx = threadIdx.x; idx < kMaxR * kMaxR; idx += blockDim.x) {
+    int s = idx / kMaxR, t = idx % kMaxR;
+    if (s < r && t < r) {
+      double g = G[(size_t)(on + s) * ldg + on + t];
+      v[0] += fmax(wk.lam[nw][s], 0.0) * fmax(wk.lam[nw][t], 0.0) * g * g;
+    }
+    if (s < ro && t < ro) {
+      double g = G[(size_t)(oo + s) * ldg + oo + t];
+      v[1] += fmax(wk.lam[od][s], 0.0) * fmax(wk.lam[od][t], 0.0) * g * g;
+    }
+    if (s < r && t < ro) {
+      double g = G[(size_t)(on + s) * ldg + oo + t];
+      v[2] += fmax(wk.lam[nw][s], 0.0) * fmax(wk.lam[od][t], 0.0) * g * g;
+    }
+  }
+  block_sum<3>(v, sh);
+  if (threadIdx.x != 0) return;
+  const double alpha = pb.alpha;
+  const double x1 = v[0], x0 = v[1], x10 = v[2];
+  const double dX2 = fmax(x1 + x0 - 2.0 * x10, 0.0);
+  const double ed2 = ctl->red_dual[0];
+  const double cross = ctl->red_dual[1];
+  const double ms2 = ctl->red_dvals[0];
+  // ||dX/alpha - M*(dy)||^2 = ||dX||^2/alpha^2 - 2/alpha <dX, M*(dy)> + ||M*(dy)||^2
+  const double ep2 = dX2 / (alpha * alpha) - 2.0 * cross / alpha + ms2;
+  const double eps_p = sqrt(fmax(ep2, 0.0));
+  const double eps_d = sqrt(fmax(ed2, 0.0));
+  const double pobj = ctl->red_dual[3];
+  const double dobj = -ctl->red_dual[2];
+  const double rel_p = eps_p / (1.0 + pb.normC);
+  const double rel_d = eps_d / (1.0 + pb.normRhs);
+  const double rel_gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
+  const double normX = sqrt(fmax(x1, 0.0));
+  const double lam_r = wk.lam[nw][r - 1];
+  const int n = pb.n;
+  const int it = ctl->it + 1;
+  ctl->it = it;
+  ctl->eps_p = eps_p;
+  ctl->eps_d = eps_d;
+  ctl->rel_p = rel_p;
+  ctl->rel_d = rel_d;
+  ctl->rel_gap = rel_gap;
+  ctl->pobj = pobj;
+  ctl->dobj = dobj;
+  ctl->lam_r = lam_r;
+  ctl->normX = normX;
+  ctl->matvecs += 1;  // warm-start product of the next iteration
+  const double comb = eps_p + eps_d;
+  const int win = ctl->window;
+  const double old = ctl->hist[it % win];
+  ctl->hist[it % win] = comb;
+  // projection tolerance for the next iteration: tighter as the residuals fall
+  if (ctl->lz_tol_fixed > 0.0) ctl->lz_tol = ctl->lz_tol_fixed;
+  else ctl->lz_tol = fmin(1e-3, fmax(2e-6, 0.05 * fmax(rel_p, rel_d)));
+  int status = ST_RUNNING;
+  if (!(comb == comb) || !(pobj == pobj)) {
+    status = ST_NUMERIC;
+  } else {
+    const bool conv = fmax(rel_p, fmax(rel_d, rel_gap)) <= ctl->tol;
+    const bool rank_ok = (r >= n) || ctl->full_eig ||
+                         (sqrt((double)(n - r)) * fmax(lam_r, 0.0) <= ctl->eps_lambda * fmax(1.0, normX));
+    bool grow = false;
+    if (conv && rank_ok) {
+      status = ST_CONVERGED;
+    } else if (conv) {
+      ctl->saved += 1;  // feasible (X_[r], y_[r]) of Alg. 2
+      grow = true;
+    } else if (it - ctl->k_change >= win && comb >= old) {
+      grow = !rank_ok;
+    }
+    if (grow && !ctl->fixed_rank) {
+      if (r >= ctl->max_rank || r >= n) status = ST_STALLED_MAX_RANK;
+      else status = ST_RANK_CHANGE;
+    }
+    if (status == ST_RUNNING && it >= ctl->it_stop) status = ST_PAUSE;
+  }
+  ctl->status = status;
+  ctl->r_old = r;
+  ctl->par = nw;       // X^{k+1} becomes the current iterate
+  ctl->lz_done = 0;    // next projection starts
+  ctl->lz_cycle = 0;
+  if (use_cond) cudaGraphSetConditional(cond, status == ST_RUNNING ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// rebuild: S = V Lambda_+ V^T - alpha (D + shift 11^T)   (64 x 64 tiles)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_rebuild(DevProblem pb, DevWork wk, int r, int sel) {
+  extern __shared__ float smr[];
+  const int ldr = r + 1;
+  float* Ap = smr;                    // kTile x (r+1): lambda_+ scaled rows of V
+  float* Bq = Ap + kTile * ldr;       // kTile x (r+1)
+  float* Tl = Bq + kTile * ldr;       // kTile x (kTile+1)
+  const int cur = sel ? 1 - wk.ctl->par : wk.ctl->par;
+  const float* V = wk.Vrm[cur];
+  const double* lam = wk.lam[cur];
+  const int tid = threadIdx.x;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  const int p0 = bi * kTile, q0 = bj * kTile;
+  const int n = pb.n;
+  for (int idx = tid; idx < kTile * r; idx += blockDim.x) {
+    int i = idx / r, t = idx % r;
+    float lp = (float)fmax(lam[t], 0.0);
+    Ap[i * ldr + t] = (p0 + i < n) ? lp * V[(size_t)(p0 + i) * wk.ldv + t] : 0.f;
+    Bq[i * ldr + t] = (q0 + i < n) ? V[(size_t)(q0 + i) * wk.ldv + t] : 0.f;
+  }
+  __syncthreads();
+  const int ty = tid / 16, tx = tid % 16;
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  for (int t = 0; t < r; ++t) {
+    float av[4], bv[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) av[a] = Ap[(ty + 16 * a) * ldr + t];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = Bq[(tx + 16 * b) * ldr + t];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+  }
+  const float ash = (float)(pb.alpha * wk.dshift[0]);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) Tl[(ty + 16 * a) * (kTile + 1) + tx + 16 * b] = acc[a][b] - ash;
+  __syncthreads();
+  const int tile = bi * pb.ntile + bj;
+  for (int e = pb.tile_ptr[tile] + tid; e < pb.tile_ptr[tile + 1]; e += blockDim.x) {
+    int loc = pb.tile_loc[e];
+    Tl[(loc / kTile) * (kTile + 1) + loc % kTile] -= (float)(pb.alpha * wk.D[pb.tile_u[e]]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kTile * kTile; idx += blockDim.x) {
+    int i = idx / kTile, j = idx % kTile;
+    if (p0 + i < n && q0 + j < n) wk.S[(size_t)(p0 + i) * wk.lds + q0 + j] = Tl[i * (kTile + 1) + j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__global__ void k_copy_cols(const float* src, int lds_, float* dst, int ldd, int n, int k,
+                            const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * k) return;
+  int c = (int)(idx / n), i = (int)(idx % n);
+  dst[(size_t)c * ldd + i] = src[(size_t)c * lds_ + i];
+}
+
+// column-major factor slot of the new iterate <- first w columns of Q
+__global__ void k_save_factor_cm(DevWork wk, float* Vcm, int n, int w) {
+  const int nw = 1 - wk.ctl->par;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n * kMaxR) return;
+  int c = (int)(idx / n), i = (int)(idx % n);
+  Vcm[(size_t)(nw * kMaxR + c) * wk.ldq + i] = (c < w) ? wk.Q[(size_t)c * wk.ldq + i] : 0.f;
+}
+
+// Full projection (n <= 128): eigenvectors of S from the dense Jacobi solve
+// become the factors of the new iterate (all n of them).
+__global__ void k_full_eig_factors(DevWork wk, int n) {
+  Ctl* ctl = wk.ctl;
+  const int nw = 1 - ctl->par;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * kMaxR; idx += gridDim.x * blockDim.x) {
+    int i = idx / kMaxR, t = idx % kMaxR;
+    float v = (t < n) ? wk.Y[(size_t)t * kMaxK + i] : 0.f;
+    wk.Vrm[nw][(size_t)i * wk.ldv + t] = v;
+    if (t < n) wk.Q[(size_t)t * wk.ldq + i] = v;
+  }
+  if (blockIdx.x == 0) {
+    for (int t = threadIdx.x; t < kMaxR; t += blockDim.x) {
+      double cs = 0.0;
+      if (t < n)
+        for (int i = 0; i < n; ++i) cs += (double)wk.Y[(size_t)t * kMaxK + i];
+      wk.lam[nw][t] = (t < n) ? wk.theta[t] : 0.0;
+      wk.colsum[nw][t] = cs;
+    }
+    if (threadIdx.x == 0) {
+      ctl->lz_done = 1;
+      ctl->lz_res = 0.0;
+    }
+  }
+}
+
+__global__ void k_s_to_t(const float* S, int lds, int n, double* T) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * n) return;
+  int i = idx / n, j = idx % n;
+  T[idx] = (double)S[(size_t)i * lds + j];
+}
+
+__global__ void k_iter_begin(cudaGraphConditionalHandle inner, int use_cond) {
+  if (use_cond) cudaGraphSetConditional(inner, 1u);
+}
+
+__global__ void k_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change) {
+  ctl->status = status;
+  ctl->it_stop = it_stop;
+  ctl->r = r;
+  ctl->w = w;
+  ctl->K = K;
+  if (k_change >= 0) ctl->k_change = k_change;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static size_t ritz_smem(int K, int w) {
+  return ((size_t)2 * RZ_RB * (K + 1) + (size_t)K * w + (size_t)2 * RZ_RB * (w + 1)) * sizeof(float);
+}
+static size_t rebuild_smem(int r) {
+  return ((size_t)2 * kTile * (r + 1) + (size_t)kTile * (kTile + 1)) * sizeof(float);
+}
+
+void init_pdhg_attributes() {
+  cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_smem(kMaxK, kMaxW));
+  cudaFuncSetAttribute(k_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rebuild_smem(kMaxR));
+}
+
+void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
+                 cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+  int blocks = (n + RZ_RB - 1) / RZ_RB;
+  k_ritz<<<blocks, 256, ritz_smem(K, w), st>>>(wk, n, K, w, r, s_steps, cond, use_cond);
+}
+
+void launch_mx(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
+  if (pb.n_chunks == 0) return;
+  int blocks = (pb.n_chunks * 32 + 255) / 256;
+  k_mx<<<blocks, 256, 0, st>>>(pb, wk, r);
+}
+
+void launch_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
+  int blocks = (pb.m + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  k_dual<<<blocks, 256, 0, st>>>(pb, wk, r);
+}
+
+void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st) {
+  int blocks = (pb.nU + 255) / 256;
+  if (blocks < 1) blocks = 1;
+  k_dvals<<<blocks, 256, 0, st>>>(pb, wk);
+}
+
+void launch_control(const DevProblem& pb, const DevWork& wk, const double* G,
+                    cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+  k_control<<<1, 256, 0, st>>>(pb, wk, G, cond, use_cond);
+}
+
+void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st) {
+  dim3 grid(pb.ntile, pb.ntile);
+  int rr = r < 1 ? 1 : r;
+  k_rebuild<<<grid, 256, rebuild_smem(rr), st>>>(pb, wk, r, sel);
+}
+
+void launch_copy_cols(const float* src, int lds, float* dst, int ldd, int n, int k, const int* skip,
+                      cudaStream_t st) {
+  size_t total = (size_t)n * k;
+  k_copy_cols<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, lds, dst, ldd, n, k, skip);
+}
+
+void launch_save_factor(const DevWork& wk, float* Vcm, int n, int w, cudaStream_t st) {
+  size_t total = (size_t)n * kMaxR;
+  k_save_factor_cm<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(wk, Vcm, n, w);
+}
+
+void launch_full_eig_factors(const DevWork& wk, int n, cudaStream_t st) {
+  k_full_eig_factors<<<32, 256, 0, st>>>(wk, n);
+}
+
+void launch_s_to_t(const float* S, int lds, int n, double* T, cudaStream_t st) {
+  k_s_to_t<<<(n * n + 255) / 256, 256, 0, st>>>(S, lds, n, T);
+}
+
+void launch_iter_begin(const DevWork& wk, cudaGraphConditionalHandle inner, int use_cond,
+                       cudaStream_t st) {
+  (void)wk;
+  k_iter_begin<<<1, 1, 0, st>>>(inner, use_cond);
+}
+
+void launch_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change,
+                    cudaStream_t st) {
+  k_ctl_set<<<1, 1, 0, st>>>(ctl, status, it_stop, r, w, K, k_change);
+}
+
+}  // namespace psdp

@@ -1,0 +1,174 @@
+// psdp.cuh — internal types and kernel launchers of the GB300 LR-PD-SDP library.
+//
+// Device state of one solver handle.  The iteration of Alg. 2 is split into
+// kernels that read their dynamic sizes (rank, block width, parity of the
+// ping-pong buffers, convergence flags) from a device control block `Ctl`, so
+// that one iteration can be captured once as a CUDA graph and replayed under a
+// conditional WHILE node without host round trips.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psdp {
+
+constexpr int kMaxWindow = 1024;  // longest stall window l (Sec. 3.2)
+constexpr int kMaxK = 128;        // largest Rayleigh-Ritz basis (one-CTA Jacobi)
+constexpr int kMaxW = 64;         // largest Lanczos block width
+constexpr int kFullEigMax = 128;  // n up to which the projection uses dense Jacobi
+constexpr int kTile = 64;         // rebuild tile edge
+constexpr int kRedSlots = 16;     // scalar reductions per kernel
+constexpr int kMaxR = 128;        // largest factor rank held (full projection up to n = 128)
+
+enum Status : int {
+  ST_CONVERGED = 0,
+  ST_MAX_ITER = 1,
+  ST_TIME_LIMIT = 2,
+  ST_STALLED_MAX_RANK = 3,
+  ST_NUMERIC = 4,
+  ST_RUNNING = 5,
+  ST_RANK_CHANGE = 6,  // the controller asked for r <- 2r; the host regrows the basis
+  ST_PAUSE = 7,        // reached the host-set iteration bound
+};
+
+// Device control block (one per handle).
+struct Ctl {
+  int it;            // completed PDHG iterations
+  int par;           // buffer index holding the current iterate X^k
+  int r;             // target rank
+  int w;             // Lanczos block width
+  int K;             // Rayleigh-Ritz basis size
+  int status;
+  int lz_done;       // projection of the current iteration converged
+  int lz_cycle;      // restart cycles run in the current iteration
+  int k_change;      // iteration of the last rank change
+  int it_stop;       // pause after this many iterations
+  int r_old;         // rank of X^k (differs from r right after a rank change)
+  int rank_changes;
+  int saved;         // feasible (X_[r], y_[r]) pairs seen (Alg. 2)
+  int full_eig;      // 1: exact projection (Alg. 1)
+  int window;
+  int max_rank;
+  int max_cycles;
+  int fixed_rank;    // 1: never change r (building-block use)
+  int pad0, pad1;
+  long long matvecs;
+  long long lz_cycles_total;
+  long long lz_unconverged;
+  double tol, eps_lambda, lz_tol_fixed, lz_tol;
+  double eps_p, eps_d, rel_p, rel_d, rel_gap, pobj, dobj, lam_r, normX, lz_res;
+  double red_dual[kRedSlots];
+  double red_dvals[kRedSlots];
+  double hist[kMaxWindow];
+};
+
+// Problem data on the device (row-scaled).  Constraint rows 0..m-1 plus the
+// objective C as row m ("extended" operator) so tr(CX) comes out of M(X).
+struct DevProblem {
+  int n, m, m_eq;
+  int nnz_ext;                 // entries of the extended rows
+  const int* dense_of_row;     // m: index into dense_row / dense_a, or -1
+  const int* ent_p;            // entry row index p (p <= q)
+  const int* ent_q;
+  const double* ent_a;         // a, times 2 off the diagonal: tr(A X) = sum a_eff X_pq
+  int n_chunks;                // work chunks of <= kChunk entries of one row
+  const int* chunk_beg;
+  const int* chunk_end;
+  const int* row_chunk;        // m + 2: chunks of row i are [row_chunk[i], row_chunk[i+1])
+  const double* rhs;           // m (scaled)
+  int n_dense;                 // structured rows a * 11^T
+  const int* dense_row;
+  const double* dense_a;
+  // union pattern of C and all A_i (upper triangle), for D = C + M*(y)
+  int nU;
+  const int* u_p;
+  const int* u_q;
+  const double* u_c;           // C entry (0 where C has none)
+  const int* u_ptr;            // nU + 1
+  const int* u_row;            // constraint row of each contribution
+  const double* u_a;           // its (scaled) matrix entry value
+  // rebuild tiles: entries of the (full, both triangles) pattern per 64x64 tile
+  int ntile;                   // tiles per dimension
+  const int* tile_ptr;         // ntile*ntile + 1
+  const int* tile_loc;         // local offset lr*64 + lc
+  const int* tile_u;           // union entry index
+  double alpha;
+  double normC, normRhs;       // ||C||_F, ||rhs||_2 (scaled problem)
+  const double* C_dense;       // dense C (row-major n x n) or nullptr
+};
+
+// Work buffers.
+struct DevWork {
+  float* S;  int lds;          // n x n row-major, row stride lds
+  float* Q;  float* W;  int ldq;  // n x kMaxK column-major Lanczos basis and S*Q
+  float* Vrm[2];  int ldv;     // X factors, n x ldv row-major (ping-pong by Ctl::par), ldv = kMaxR
+  double* lam[2];              // their eigenvalues (unclamped), ldv each
+  double* colsum[2];           // column sums of Vrm (structured dense rows)
+  double* y;                   // current dual (scaled problem, algorithm sign)
+  double* dy;                  // last dual change
+  double* mx[2];               // M_ext(X) for both buffers (m + 1)
+  double* chunk_part;          // per-chunk partial sums
+  double* D;                   // D = C + M*(y) on the union pattern
+  double* dshift;              // [0]: sum over dense rows a*y, [1]: same with dy
+  double* part;                // generic per-CTA partials
+  double* H;                   // small dense FP64 results (Gram, T)
+  float* Hf;                   // FP32 copy / R^{-1}
+  int* flags;                  // deficient-column flags
+  float* Y;  double* theta;    // Ritz solve output (kMaxK x kMaxK), values
+  double* ritz_part;           // partials of the Ritz kernel
+  unsigned* counters;          // last-block counters (512 per kernel kind)
+  Ctl* ctl;
+};
+
+enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_NUM };
+
+// ---------------------------------------------------------------------------
+// launchers (k_lanczos.cu)
+// ---------------------------------------------------------------------------
+void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
+                         int k, const int* skip, cudaStream_t st);
+void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
+                         cudaStream_t st);
+// H = A^T B (ka x kb, FP64 row-major) with deterministic block reduction.
+// With act > 0 only output tiles whose row and column offsets modulo `slot`
+// fall below `act` are computed (Gram of a few columns of each factor slot).
+void launch_gram(const float* A, int lda, int ka, const float* B, int ldb, int kb, int n,
+                 double* H, double* part, unsigned* counter, const int* skip, cudaStream_t st,
+                 int act = 0, int slot = 0);
+// Z -= A * H
+void launch_block_update(float* Z, int ldz, int kb, const float* A, int lda, int ka, const double* H,
+                         int n, const int* skip, cudaStream_t st);
+// Cholesky of G (w x w), writes R^{-1} (FP32) and deficient flags.
+void launch_chol_inv(const double* G, int w, float* Rinv, int* flags, const int* skip, cudaStream_t st);
+// Z <- Z * R^{-1}; deficient columns replaced by pseudo-random vectors.
+void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* flags, int n,
+                       unsigned long long seed, const int* skip, cudaStream_t st);
+void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
+                    const int* skip, cudaStream_t st);
+void launch_sym_eig_f64(const double* T, int K, double* theta, double* Y, int ldy, cudaStream_t st);
+void init_lanczos_attributes();
+
+// ---------------------------------------------------------------------------
+// launchers (k_pdhg.cu)
+// ---------------------------------------------------------------------------
+void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
+                 cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+void launch_mx(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
+void launch_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
+void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st);
+void launch_control(const DevProblem& pb, const DevWork& wk, const double* G,
+                    cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+// sel = 0: factors of the current iterate (Ctl::par); sel = 1: the other buffer.
+void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st);
+void launch_copy_cols(const float* src, int lds, float* dst, int ldd, int n, int k, const int* skip,
+                      cudaStream_t st);
+void launch_save_factor(const DevWork& wk, float* Vcm, int n, int w, cudaStream_t st);
+void launch_full_eig_factors(const DevWork& wk, int n, cudaStream_t st);
+void launch_s_to_t(const float* S, int lds, int n, double* T, cudaStream_t st);
+void launch_iter_begin(const DevWork& wk, cudaGraphConditionalHandle inner, int use_cond,
+                       cudaStream_t st);
+void launch_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change,
+                    cudaStream_t st);
+void init_pdhg_attributes();
+
+}  // namespace psdp

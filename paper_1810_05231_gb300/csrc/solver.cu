@@ -1,0 +1,691 @@
+// solver.cu — device memory, kernel sequencing and CUDA-graph capture of the
+// LR-PD-SDP iteration (Alg. 2; Alg. 1 when every eigenpair is kept).
+//
+// One iteration is:
+//   warm-start product  W[:, :w] = S^k Q[:, :w]        (Q[:, :w]: Ritz vectors of S^{k-1})
+//   restart cycles       block Krylov steps + Rayleigh-Ritz until the r wanted
+//                        Ritz pairs have converged                  (aproj, Sec. 3.1)
+//   M(X^{k+1})           from the factors                           (dual step part 1)
+//   dual step            equality / inequality split                (Eq. resolvent_1)
+//   D = C + M*(y^{k+1})  and ||M*(dy)||
+//   controller           residuals (Sec. 2.2), stop test, rank rule (Sec. 3.2)
+//   rebuild              S^{k+1} = X^{k+1} - alpha D                (primal step input)
+// Inside a CUDA graph the restart cycles sit under a conditional WHILE node
+// (set by the Ritz kernel) and the iterations under an outer WHILE node (set
+// by the controller), so a whole batch of iterations runs without the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solver.h"
+
+namespace psdp {
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return fail(PROXSDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+void init_kernel_attributes() {
+  static bool done = false;
+  if (done) return;
+  init_pdhg_attributes();
+  init_lanczos_attributes();
+  done = true;
+}
+
+Solver::~Solver() { free_all(); }
+
+void Solver::free_all() {
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+  if (ctl_host) cudaFreeHost(ctl_host);
+  ctl_host = nullptr;
+  if (st_aux) cudaStreamDestroy(st_aux);
+  st_aux = nullptr;
+  if (own_stream && st) cudaStreamDestroy(st);
+  st = nullptr;
+  own_stream = false;
+}
+
+template <class T>
+static cudaError_t dalloc(std::vector<void*>& allocs, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+template <class T>
+static cudaError_t dupload(std::vector<void*>& allocs, const T** p, const std::vector<T>& v,
+                           cudaStream_t st) {
+  T* q = nullptr;
+  cudaError_t e = dalloc(allocs, &q, v.size());
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpyAsync(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+  *p = q;
+  return e;
+}
+
+#define CKA(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ == cudaErrorMemoryAllocation) return fail(PROXSDP_ERR_OOM, "device allocation failed"); \
+    if (e_ != cudaSuccess) return fail(PROXSDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int Solver::upload(const HostProblem& h, bool alloc_S) {
+  // release a previous problem
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  graphs.clear();
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+  has_problem = false;
+  has_iterate = false;
+  hp = h;
+  const int n = h.n;
+  DevProblem& P = pb;
+  P = DevProblem{};
+  P.n = n;
+  P.m = h.m;
+  P.m_eq = h.m_eq;
+  P.nnz_ext = (int)h.ent_p.size();
+  CKA(dupload(allocs, &P.ent_p, h.ent_p, st));
+  CKA(dupload(allocs, &P.ent_q, h.ent_q, st));
+  CKA(dupload(allocs, &P.ent_a, h.ent_a, st));
+  P.n_chunks = (int)h.chunk_beg.size();
+  CKA(dupload(allocs, &P.chunk_beg, h.chunk_beg, st));
+  CKA(dupload(allocs, &P.chunk_end, h.chunk_end, st));
+  CKA(dupload(allocs, &P.row_chunk, h.row_chunk, st));
+  CKA(dupload(allocs, &P.rhs, h.rhs, st));
+  P.n_dense = (int)h.dense_row.size();
+  CKA(dupload(allocs, &P.dense_row, h.dense_row, st));
+  CKA(dupload(allocs, &P.dense_a, h.dense_a, st));
+  CKA(dupload(allocs, &P.dense_of_row, h.dense_of_row, st));
+  P.nU = (int)h.u_p.size();
+  CKA(dupload(allocs, &P.u_p, h.u_p, st));
+  CKA(dupload(allocs, &P.u_q, h.u_q, st));
+  CKA(dupload(allocs, &P.u_c, h.u_c, st));
+  CKA(dupload(allocs, &P.u_ptr, h.u_ptr, st));
+  CKA(dupload(allocs, &P.u_row, h.u_row, st));
+  CKA(dupload(allocs, &P.u_a, h.u_a, st));
+  P.ntile = h.ntile;
+  CKA(dupload(allocs, &P.tile_ptr, h.tile_ptr, st));
+  CKA(dupload(allocs, &P.tile_loc, h.tile_loc, st));
+  CKA(dupload(allocs, &P.tile_u, h.tile_u, st));
+  P.alpha = h.alpha;
+  P.normC = h.normC;
+  P.normRhs = h.normRhs;
+  P.C_dense = nullptr;
+
+  DevWork& Wk = wk;
+  Wk = DevWork{};
+  const int ld = (n + 31) / 32 * 32;
+  Wk.lds = ld;
+  Wk.ldq = ld;
+  Wk.ldv = kMaxR;
+  if (alloc_S) CKA(dalloc(allocs, &Wk.S, (size_t)n * ld));
+  CKA(dalloc(allocs, &Wk.Q, (size_t)ld * kMaxK));
+  CKA(dalloc(allocs, &Wk.W, (size_t)ld * kMaxK));
+  for (int b = 0; b < 2; ++b) {
+    CKA(dalloc(allocs, &Wk.Vrm[b], (size_t)n * kMaxR));
+    CKA(dalloc(allocs, &Wk.lam[b], kMaxR));
+    CKA(dalloc(allocs, &Wk.colsum[b], kMaxR));
+    CKA(dalloc(allocs, &Wk.mx[b], (size_t)h.m + 1));
+  }
+  CKA(dalloc(allocs, &Wk.y, (size_t)h.m));
+  CKA(dalloc(allocs, &Wk.dy, (size_t)h.m));
+  CKA(dalloc(allocs, &Wk.chunk_part, std::max<size_t>(h.chunk_beg.size(), 1)));
+  CKA(dalloc(allocs, &Wk.D, std::max<size_t>(h.u_p.size(), 1)));
+  CKA(dalloc(allocs, &Wk.dshift, 4));
+  CKA(dalloc(allocs, &Wk.part, (size_t)1 << 20));
+  CKA(dalloc(allocs, &Wk.H, (size_t)kMaxK * kMaxK));
+  CKA(dalloc(allocs, &Wk.Hf, (size_t)kMaxW * kMaxW));
+  CKA(dalloc(allocs, &Wk.flags, kMaxW));
+  CKA(dalloc(allocs, &Wk.Y, (size_t)kMaxK * kMaxK));
+  CKA(dalloc(allocs, &Wk.theta, kMaxK));
+  CKA(dalloc(allocs, &Wk.ritz_part, ((size_t)(n + 31) / 32 + 1) * 4 * kMaxW));
+  CKA(dalloc(allocs, &Wk.counters, (size_t)CNT_NUM * 512));
+  CKA(dalloc(allocs, &Wk.ctl, 1));
+  CKA(dalloc(allocs, &Vcm, (size_t)ld * 2 * kMaxR));
+  CKA(dalloc(allocs, &Hx, (size_t)4 * kMaxR * kMaxR));
+  CK(cudaMemsetAsync(Wk.counters, 0, sizeof(unsigned) * CNT_NUM * 512, st));
+  CK(cudaMemsetAsync(Wk.Q, 0, sizeof(float) * (size_t)ld * kMaxK, st));
+  CK(cudaMemsetAsync(Wk.W, 0, sizeof(float) * (size_t)ld * kMaxK, st));
+  CK(cudaMemsetAsync(Vcm, 0, sizeof(float) * (size_t)ld * 2 * kMaxR, st));
+  if (alloc_S) CK(cudaMemsetAsync(Wk.S, 0, sizeof(float) * (size_t)n * ld, st));
+  CK(cudaStreamSynchronize(st));
+  has_problem = true;
+  return PROXSDP_OK;
+}
+
+// Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s for rank r.
+void Solver::dims(int rr, int& w, int& K, int& s) const {
+  const int n = hp.n;
+  const int b = std::max(1, set.block_size);
+  if (n <= kFullEigMax || set.full_eig) {
+    w = n;
+    K = n;
+    s = 0;
+    return;
+  }
+  int g = set.guard > 0 ? set.guard : std::max(8, rr / 4);
+  w = ((rr + g + b - 1) / b) * b;
+  w = std::min(w, kMaxW);
+  if (set.lanczos_steps > 0) s = set.lanczos_steps;
+  else s = std::max(1, 64 / w - 1);
+  while ((s + 1) * w > kMaxK && s > 1) --s;
+  K = (s + 1) * w;
+}
+
+int Solver::set_ctl_fields(int status, int it_stop, int rr, int w, int K, int k_change) {
+  launch_ctl_set(wk.ctl, status, it_stop, rr, w, K, k_change, st);
+  CK(cudaGetLastError());
+  return PROXSDP_OK;
+}
+
+// Orthonormalise Z = Q[:, c0:c0+w] against Q[:, :c0] and within itself:
+// two passes of (classical Gram-Schmidt, Cholesky QR); columns found
+// dependent in the first pass are refilled with pseudo-random vectors.
+static void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed,
+                         const int* skip, cudaStream_t st) {
+  float* Z = wk.Q + (size_t)c0 * wk.ldq;
+  unsigned* cnt = wk.counters + CNT_GRAM * 512;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (c0 > 0) {
+      launch_gram(wk.Q, wk.ldq, c0, Z, wk.ldq, w, n, wk.H, wk.part, cnt, skip, st);
+      launch_block_update(Z, wk.ldq, w, wk.Q, wk.ldq, c0, wk.H, n, skip, st);
+    }
+    launch_gram(Z, wk.ldq, w, Z, wk.ldq, w, n, wk.H, wk.part, cnt, skip, st);
+    launch_chol_inv(wk.H, w, wk.Hf, wk.flags, skip, st);
+    launch_apply_rinv(Z, wk.ldq, w, wk.Hf, wk.flags, n, seed * 131ULL + (unsigned long long)(pass * 7 + c0),
+                      skip, st);
+  }
+}
+
+static void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
+                          unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
+                          cudaStream_t st) {
+  const int* skip = &wk.ctl->lz_done;
+  for (int j = 1; j <= s; ++j) {
+    launch_copy_cols(wk.W + (size_t)(j - 1) * w * wk.ldq, wk.ldq, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
+                     n, w, skip, st);
+    enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st);
+    launch_block_matvec(wk.S, wk.lds, n, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
+                        wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st);
+  }
+  launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
+  launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st);
+  launch_ritz(wk, n, K, w, r, s, cond, use_cond, st);
+}
+
+// Enqueue one iteration on `st` (direct launches or inside a capture).
+int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditionalHandle outer,
+                              cudaGraphConditionalHandle inner) {
+  const int n = hp.n;
+  const int use = in_graph ? 1 : 0;
+  if (k.full) {
+    launch_s_to_t(wk.S, wk.lds, n, wk.H, st);
+    launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, st);
+    launch_full_eig_factors(wk, n, st);
+  } else {
+    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st);
+    if (in_graph) {
+      launch_iter_begin(wk, inner, 1, st);
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t g;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* ed = nullptr;
+      size_t nd = 0;
+      CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, &ed, &nd));
+      cudaGraphNodeParams p = {};
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = inner;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      cudaGraphNode_t node;
+      CK(cudaGraphAddNode(&node, g, deps, ed, nd, &p));
+      CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      cudaGraph_t body = p.conditional.phGraph_out[0];
+      CK(cudaStreamBeginCaptureToGraph(st_aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 1, st_aux);
+      CK(cudaStreamEndCapture(st_aux, &body));
+    } else {
+      for (int c = 0; c < std::max(1, set.lanczos_max_cycles); ++c)
+        enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed + 977ULL * (unsigned long long)c, inner, 0, st);
+    }
+  }
+  launch_save_factor(wk, Vcm, n, k.full ? n : k.w, st);
+  launch_mx(pb, wk, k.r, st);
+  launch_dual(pb, wk, k.r, st);
+  launch_dvals(pb, wk, st);
+  const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
+  launch_gram(Vcm, wk.ldq, 2 * kMaxR, Vcm, wk.ldq, 2 * kMaxR, n, Hx, wk.part,
+              wk.counters + CNT_CTL * 512, nullptr, st, act, kMaxR);
+  launch_control(pb, wk, Hx, outer, use, st);
+  launch_rebuild(pb, wk, k.r, 0, st);
+  CK(cudaGetLastError());
+  return PROXSDP_OK;
+}
+
+int Solver::get_graph(const GraphKey& k, cudaGraphExec_t* out) {
+  auto it = graphs.find(k);
+  if (it != graphs.end()) {
+    *out = it->second;
+    return PROXSDP_OK;
+  }
+  cudaGraph_t g;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle outer, inner = 0;
+  CK(cudaGraphConditionalHandleCreate(&outer, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = outer;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  if (!k.full) CK(cudaGraphConditionalHandleCreate(&inner, body, 1, cudaGraphCondAssignDefault));
+  CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  int rc = enqueue_iteration(k, true, outer, inner);
+  cudaGraph_t body2;
+  cudaError_t ce = cudaStreamEndCapture(st, &body2);
+  if (rc != PROXSDP_OK) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  if (ce != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(PROXSDP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+  }
+  cudaGraphExec_t ex;
+  cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return fail(PROXSDP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+  graphs[k] = ex;
+  *out = ex;
+  return PROXSDP_OK;
+}
+
+int Solver::read_ctl() {
+  CK(cudaMemcpyAsync(ctl_host, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PROXSDP_OK;
+}
+
+// X = 0, y = 0: S^0 = -alpha C; random orthonormal start block.
+int Solver::init_iterate_zero() {
+  const int n = hp.n;
+  CK(cudaMemsetAsync(wk.y, 0, sizeof(double) * std::max(hp.m, 1), st));
+  CK(cudaMemsetAsync(wk.dy, 0, sizeof(double) * std::max(hp.m, 1), st));
+  for (int b = 0; b < 2; ++b) {
+    CK(cudaMemsetAsync(wk.Vrm[b], 0, sizeof(float) * (size_t)n * kMaxR, st));
+    CK(cudaMemsetAsync(wk.lam[b], 0, sizeof(double) * kMaxR, st));
+    CK(cudaMemsetAsync(wk.colsum[b], 0, sizeof(double) * kMaxR, st));
+    CK(cudaMemsetAsync(wk.mx[b], 0, sizeof(double) * (hp.m + 1), st));
+  }
+  CK(cudaMemsetAsync(Vcm, 0, sizeof(float) * (size_t)wk.ldq * 2 * kMaxR, st));
+  rank_changes = 0;
+  r = std::max(1, std::min(set.full_eig ? n : set.rank_init, n));
+  if (!set.full_eig) r = std::min(r, set.max_rank);
+  int w, K, s;
+  dims(r, w, K, s);
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  c.par = 0;
+  c.r = r;
+  c.r_old = r;
+  c.w = w;
+  c.K = K;
+  c.status = ST_RUNNING;
+  c.full_eig = set.full_eig ? 1 : 0;
+  c.window = std::max(1, std::min(set.window, kMaxWindow));
+  c.max_rank = set.full_eig ? n : std::min(set.max_rank, n);
+  c.max_cycles = std::max(1, set.lanczos_max_cycles);
+  c.tol = set.tol;
+  c.eps_lambda = set.eps_lambda > 0 ? set.eps_lambda : set.tol;
+  c.lz_tol_fixed = set.lanczos_tol;
+  c.lz_tol = set.lanczos_tol > 0 ? set.lanczos_tol : 1e-3;
+  for (int i = 0; i < kMaxWindow; ++i) c.hist[i] = INFINITY;
+  std::memcpy(ctl_host, &c, sizeof(Ctl));
+  CK(cudaMemcpyAsync(wk.ctl, ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  // D = C (y = 0), S^0 = -alpha C
+  launch_dvals(pb, wk, st);
+  launch_rebuild(pb, wk, 1, 0, st);
+  if (!(n <= kFullEigMax || set.full_eig)) {
+    launch_random_block(wk.Q, wk.ldq, n, 0, w, seed, st);
+    enqueue_orth(wk, n, 0, w, seed, nullptr, st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  has_iterate = true;
+  return PROXSDP_OK;
+}
+
+// Grow the Krylov block from w_old to w_new columns: new columns are random
+// vectors orthogonalised against the current Ritz vectors.
+int Solver::grow_basis(int w_old, int w_new) {
+  if (w_new <= w_old || hp.n <= kFullEigMax || set.full_eig) return PROXSDP_OK;
+  launch_random_block(wk.Q, wk.ldq, hp.n, w_old, w_new - w_old, seed + 31ULL * (unsigned long long)w_new, st);
+  enqueue_orth(wk, hp.n, w_old, w_new - w_old, seed + 7ULL * (unsigned long long)w_new, nullptr, st);
+  CK(cudaGetLastError());
+  return PROXSDP_OK;
+}
+
+// Run iterations until convergence / a cap.  iters_cap < 0: no cap beyond
+// max_iter.  With stop_on_converge == false exactly iters_cap iterations run
+// (the rank rule still acts).
+int Solver::run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info) {
+  if (!has_problem) return fail(PROXSDP_ERR_BAD_STATE, "no problem loaded");
+  const int n = hp.n;
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  CK(cudaMemcpyAsync(ctl_host, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  int it0 = ctl_host->it;
+  int64_t limit = set.max_iter;
+  if (iters_cap >= 0) limit = std::min<int64_t>(limit, it0 + iters_cap);
+  int final_status = ST_MAX_ITER;
+  const bool graphs_on = set.use_graphs != 0;
+  for (;;) {
+    int it = ctl_host->it;
+    if (it >= limit) {
+      final_status = ST_MAX_ITER;
+      break;
+    }
+    double elapsed = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (set.time_limit_s > 0 && elapsed > set.time_limit_s) {
+      final_status = ST_TIME_LIMIT;
+      break;
+    }
+    int w, K, s;
+    dims(r, w, K, s);
+    GraphKey key{r, w, K, s, (n <= kFullEigMax || set.full_eig) ? 1 : 0};
+    int chunk = std::max(1, set.check_every);
+    int it_stop = (int)std::min<int64_t>(limit, (int64_t)it + chunk);
+    int rc = set_ctl_fields(ST_RUNNING, it_stop, r, w, K, -1);
+    if (rc) return rc;
+    if (graphs_on) {
+      cudaGraphExec_t ex;
+      rc = get_graph(key, &ex);
+      if (rc) return rc;
+      CK(cudaGraphLaunch(ex, st));
+      rc = read_ctl();
+      if (rc) return rc;
+    } else {
+      for (int i = it; i < it_stop; ++i) {
+        rc = enqueue_iteration(key, false, 0, 0);
+        if (rc) return rc;
+        rc = read_ctl();
+        if (rc) return rc;
+        if (ctl_host->status != ST_RUNNING) break;
+      }
+    }
+    const int status = ctl_host->status;
+    if (status == ST_RUNNING || status == ST_PAUSE) continue;
+    if (status == ST_CONVERGED) {
+      final_status = ST_CONVERGED;
+      if (stop_on_converge) break;
+      continue;
+    }
+    if (status == ST_RANK_CHANGE) {
+      int r_new = std::min(std::min(2 * r, n), std::max(set.max_rank, 1));
+      int w_old = w;
+      r = r_new;
+      int w2, K2, s2;
+      dims(r, w2, K2, s2);
+      rc = grow_basis(w_old, w2);
+      if (rc) return rc;
+      rc = set_ctl_fields(ST_RUNNING, it_stop, r, w2, K2, ctl_host->it);
+      if (rc) return rc;
+      rank_changes += 1;
+      continue;
+    }
+    final_status = status;  // STALLED_AT_MAX_RANK / NUMERIC
+    break;
+  }
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = read_ctl();
+  if (rc) return rc;
+  if (info) {
+    const Ctl& c = *ctl_host;
+    std::memset(info, 0, sizeof(*info));
+    info->status = final_status;
+    info->final_rank = r;
+    info->iters = c.it;
+    info->rank_changes = rank_changes;
+    info->primal_obj = c.pobj;
+    info->dual_obj = c.dobj;
+    info->rel_primal_res = c.rel_p;
+    info->rel_dual_res = c.rel_d;
+    info->rel_gap = c.rel_gap;
+    info->eps_primal = c.eps_p;
+    info->eps_dual = c.eps_d;
+    info->lambda_r = c.lam_r;
+    info->solve_seconds = ms * 1e-3;
+    info->matvecs = c.matvecs;
+    info->lanczos_cycles = c.lz_cycles_total;
+    info->lanczos_unconverged = c.lz_unconverged;
+    info->alpha = hp.alpha;
+    info->norm_M = hp.normM;
+  }
+  return PROXSDP_OK;
+}
+
+// Start the iteration from X = V diag(max(lambda,0)) V^T, y (paper's sign,
+// original row scaling).
+int Solver::set_iterate(int rr, const double* V, const double* lam, const double* y) {
+  const int n = hp.n, m = hp.m;
+  int rc = init_iterate_zero();
+  if (rc) return rc;
+  r = rr;
+  int w, K, s;
+  dims(r, w, K, s);
+  std::vector<float> vrm((size_t)n * kMaxR, 0.f), vcm((size_t)wk.ldq * kMaxR, 0.f);
+  std::vector<double> l(kMaxR, 0.0), cs(kMaxR, 0.0);
+  for (int t = 0; t < rr; ++t) {
+    l[t] = lam[t];
+    for (int i = 0; i < n; ++i) {
+      float v = (float)V[(size_t)t * n + i];
+      vrm[(size_t)i * kMaxR + t] = v;
+      vcm[(size_t)t * wk.ldq + i] = v;
+      cs[t] += (double)v;
+    }
+  }
+  // M_ext(X) of the given iterate, from the stored (FP32) factors
+  std::vector<double> mx(m + 1, 0.0);
+  for (int row = 0; row <= m; ++row) {
+    for (int c = hp.row_chunk[row]; c < hp.row_chunk[row + 1]; ++c)
+      for (int e = hp.chunk_beg[c]; e < hp.chunk_end[c]; ++e) {
+        const int p = hp.ent_p[e], q = hp.ent_q[e];
+        double x = 0.0;
+        for (int t = 0; t < rr; ++t)
+          x += std::max(l[t], 0.0) * (double)vrm[(size_t)p * kMaxR + t] * (double)vrm[(size_t)q * kMaxR + t];
+        mx[row] += hp.ent_a[e] * x;
+      }
+    if (row < m && hp.dense_of_row[row] >= 0) {
+      double sacc = 0.0;
+      for (int t = 0; t < rr; ++t) sacc += std::max(l[t], 0.0) * cs[t] * cs[t];
+      mx[row] += hp.dense_a[hp.dense_of_row[row]] * sacc;
+    }
+  }
+  std::vector<double> ya(std::max(m, 1), 0.0);
+  if (y)
+    for (int i = 0; i < m; ++i) ya[i] = -y[i] / hp.scale[i];
+  CK(cudaMemcpyAsync(wk.Vrm[0], vrm.data(), sizeof(float) * vrm.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(wk.lam[0], l.data(), sizeof(double) * kMaxR, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(wk.colsum[0], cs.data(), sizeof(double) * kMaxR, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(wk.mx[0], mx.data(), sizeof(double) * (m + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(Vcm, vcm.data(), sizeof(float) * vcm.size(), cudaMemcpyHostToDevice, st));
+  if (m > 0) CK(cudaMemcpyAsync(wk.y, ya.data(), sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(wk.dy, 0, sizeof(double) * std::max(m, 1), st));
+  CK(cudaStreamSynchronize(st));
+  // control block: current iterate in buffer 0 with rank rr
+  Ctl* c = ctl_host;
+  CK(cudaMemcpyAsync(c, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  c->par = 0;
+  c->r = rr;
+  c->r_old = rr;
+  c->w = w;
+  c->K = K;
+  c->it = 0;
+  c->k_change = 0;
+  c->status = ST_RUNNING;
+  c->max_rank = set.full_eig ? n : std::min(std::max(set.max_rank, rr), n);
+  CK(cudaMemcpyAsync(wk.ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  // S^k = X^k - alpha (C + M*(y^k)), Lanczos warm start = the given factors
+  launch_dvals(pb, wk, st);
+  launch_rebuild(pb, wk, rr, 0, st);
+  if (!(n <= kFullEigMax || set.full_eig)) {
+    CK(cudaMemcpyAsync(wk.Q, vcm.data(), sizeof(float) * (size_t)wk.ldq * std::min(rr, w),
+                       cudaMemcpyHostToDevice, st));
+    if (w > rr) {
+      launch_random_block(wk.Q, wk.ldq, n, rr, w - rr, seed + 5, st);
+      enqueue_orth(wk, n, rr, w - rr, seed + 9, nullptr, st);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  has_iterate = true;
+  return PROXSDP_OK;
+}
+
+// aproj(S, r) on caller memory: Lanczos (or dense Jacobi for n <= 128) on S,
+// then P = V diag(max(lambda,0)) V^T through the rebuild kernel.
+int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float* V, double* lambda,
+                 const proxsdp_gpu_settings& set, cudaStream_t st_in, proxsdp_gpu_info* info,
+                 std::string& err) {
+  Solver sv;
+  sv.set = set;
+  sv.set.full_eig = 0;
+  sv.seed = set.seed ? set.seed : 1;
+  sv.st = st_in;
+  sv.own_stream = false;
+  if (cudaStreamCreateWithFlags(&sv.st_aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMallocHost((void**)&sv.ctl_host, sizeof(Ctl)) != cudaSuccess) {
+    err = "stream / host allocation failed";
+    return PROXSDP_ERR_CUDA;
+  }
+  HostProblem h;
+  h.n = n;
+  h.m = 0;
+  h.m_eq = 0;
+  h.row_chunk.assign(2, 0);
+  h.dense_of_row.assign(1, -1);
+  h.ntile = (n + kTile - 1) / kTile;
+  h.tile_ptr.assign((size_t)h.ntile * h.ntile + 1, 0);
+  h.u_ptr.assign(1, 0);
+  h.alpha = 0.0;
+  int rc = sv.upload(h, false);
+  if (rc) {
+    err = sv.err;
+    return rc;
+  }
+  DevWork& wk = sv.wk;
+  wk.S = const_cast<float*>(S);
+  wk.lds = lds;
+  const bool full = n <= kFullEigMax;
+  sv.r = r;
+  int w, K, s;
+  sv.dims(r, w, K, s);
+  if (!full && r > w - 4) {
+    err = "rank too large for the Lanczos block (r <= 60)";
+    return PROXSDP_ERR_UNSUPPORTED;
+  }
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  c.par = 0;
+  c.r = r;
+  c.r_old = r;
+  c.w = w;
+  c.K = K;
+  c.status = ST_RUNNING;
+  c.max_cycles = std::max(1, set.lanczos_max_cycles);
+  c.lz_tol_fixed = set.lanczos_tol > 0 ? set.lanczos_tol : 1e-6;
+  c.lz_tol = c.lz_tol_fixed;
+  std::memcpy(sv.ctl_host, &c, sizeof(Ctl));
+  cudaError_t e = cudaMemcpyAsync(wk.ctl, sv.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, sv.st);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return PROXSDP_ERR_CUDA;
+  }
+  cudaMemsetAsync(wk.dshift, 0, 4 * sizeof(double), sv.st);
+  if (full) {
+    launch_s_to_t(S, lds, n, wk.H, sv.st);
+    launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, sv.st);
+    launch_full_eig_factors(wk, n, sv.st);
+  } else {
+    launch_random_block(wk.Q, wk.ldq, n, 0, w, sv.seed, sv.st);
+    enqueue_orth(wk, n, 0, w, sv.seed, nullptr, sv.st);
+    launch_block_matvec(S, lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, w, nullptr, sv.st);
+    for (int cyc = 0; cyc < c.max_cycles; ++cyc)
+      enqueue_cycle(wk, n, w, K, s, r, sv.seed + 1000ULL * (unsigned long long)(cyc + 1), 0, 0, sv.st);
+  }
+  if (P) {
+    DevWork out = wk;
+    out.S = P;
+    out.lds = ldp;
+    launch_rebuild(sv.pb, out, r, 1, sv.st);
+  }
+  if (V) {
+    if (full) {
+      e = cudaMemcpy2DAsync(V, sizeof(float) * n, wk.Y, sizeof(float) * kMaxK, sizeof(float) * n, r,
+                            cudaMemcpyDeviceToDevice, sv.st);
+    } else {
+      e = cudaMemcpy2DAsync(V, sizeof(float) * n, wk.Q, sizeof(float) * wk.ldq, sizeof(float) * n, r,
+                            cudaMemcpyDeviceToDevice, sv.st);
+    }
+    if (e != cudaSuccess) {
+      err = cudaGetErrorString(e);
+      return PROXSDP_ERR_CUDA;
+    }
+  }
+  if (lambda) {
+    e = cudaMemcpyAsync(lambda, wk.lam[1], sizeof(double) * r, cudaMemcpyDeviceToDevice, sv.st);
+    if (e != cudaSuccess) {
+      err = cudaGetErrorString(e);
+      return PROXSDP_ERR_CUDA;
+    }
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sv.ctl_host, wk.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sv.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(sv.st);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return PROXSDP_ERR_CUDA;
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->final_rank = r;
+    info->matvecs = full ? 0 : 1 + (int64_t)sv.ctl_host->lz_cycles_total * s;
+    info->lanczos_cycles = sv.ctl_host->lz_cycles_total;
+    info->lanczos_unconverged = sv.ctl_host->lz_unconverged;
+    info->eps_primal = sv.ctl_host->lz_res;
+    info->status = (sv.ctl_host->lz_done && sv.ctl_host->lz_unconverged == 0) ? PROXSDP_CONVERGED : PROXSDP_MAX_ITER;
+  }
+  sv.st = nullptr;  // caller's stream
+  return PROXSDP_OK;
+}
+
+int sym_eig_device(const double* T, int K, double* theta, float* Y, cudaStream_t st) {
+  launch_sym_eig(T, K, theta, Y, K, K, nullptr, st);
+  return cudaGetLastError() == cudaSuccess ? PROXSDP_OK : PROXSDP_ERR_CUDA;
+}
+
+}  // namespace psdp

@@ -1,0 +1,87 @@
+// solver.h — host-side state of a proxsdp_gpu handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/proxsdp_gpu.h"
+#include "psdp.cuh"
+
+namespace psdp {
+
+constexpr int kChunk = 128; // entries per M(X) work chunk
+
+// Problem after validation, row scaling and the layout passes (host copy).
+struct HostProblem {
+  int n = 0, m = 0, m_eq = 0;
+  std::vector<int> ent_p, ent_q;
+  std::vector<double> ent_a;  // extended rows: constraints then the objective row
+  std::vector<int> chunk_beg, chunk_end, row_chunk;
+  std::vector<double> rhs, scale;
+  std::vector<int> dense_row, dense_of_row;
+  std::vector<double> dense_a;
+  std::vector<int> u_p, u_q, u_ptr, u_row;
+  std::vector<double> u_c, u_a;
+  int ntile = 0;
+  std::vector<int> tile_ptr, tile_loc, tile_u;
+  double normM = 1.0, alpha = 0.0, normC = 0.0, normRhs = 0.0;
+};
+
+struct GraphKey {
+  int r, w, K, s, full;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(r, w, K, s, full) < std::tie(o.r, o.w, o.K, o.s, o.full);
+  }
+};
+
+struct Solver {
+  proxsdp_gpu_settings set{};
+  int device = 0;
+  cudaStream_t st = nullptr, st_aux = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool has_problem = false;
+  bool has_iterate = false;
+  HostProblem hp;
+  DevProblem pb{};
+  DevWork wk{};
+  float* Vcm = nullptr;  // column-major factor slots (2 * kMaxR columns)
+  double* Hx = nullptr;  // Gram of the factor slots
+  std::vector<void*> allocs;
+  Ctl* ctl_host = nullptr;  // pinned mirror
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  int r = 8;
+  int rank_changes = 0;
+  unsigned long long seed = 1;
+
+  ~Solver();
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  int upload(const HostProblem& h, bool alloc_S = true);
+  int init_iterate_zero();
+  int set_iterate(int r, const double* V, const double* lam, const double* y);
+  int run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info);
+  int read_ctl();
+  void dims(int r, int& w, int& K, int& s) const;
+  int grow_basis(int w_old, int w_new);
+  int enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditionalHandle outer,
+                        cudaGraphConditionalHandle inner);
+  int get_graph(const GraphKey& k, cudaGraphExec_t* out);
+  int set_ctl_fields(int status, int it_stop, int r, int w, int K, int k_change);
+  void free_all();
+};
+
+// device helpers used by the API (solver.cu)
+int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float* V, double* lambda,
+                 const proxsdp_gpu_settings& set, cudaStream_t st, proxsdp_gpu_info* info,
+                 std::string& err);
+int sym_eig_device(const double* T, int K, double* theta, float* Y, cudaStream_t st);
+void init_kernel_attributes();
+
+}  // namespace psdp

@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (float comparisons):
+* block product S Q (FP32 data, FP32 accumulation): relative Frobenius error
+  <= 2e-6 * sqrt(n)/sqrt(2000) + 1e-6 against the FP64 product;
+* small Jacobi eigensolver (FP32 rotations): eigenvalues within 2e-6 ||T||,
+  residual ||T y - theta y|| <= 1e-5 ||T||;
+* truncated projection aproj(S, r): ||P_gpu - P_ref||_F / ||P_ref||_F <= 1e-5;
+* one iteration of Alg. 2 from a shared iterate: X and y within 1e-4
+  relative, residuals within 1e-3 relative (they are differences of nearby
+  iterates);
+* converged solves: objective within 1e-4 relative of the closed form or of
+  the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import sdp_instances as si
+from oracle.sdp import Problem, normalize_rows, pd_iteration
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_05231_gb300 as p
+
+    return p
+
+
+DEV = "cuda:0"
+
+
+# ---------------------------------------------------------------------------
+# building blocks
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,k", [(1, 1), (17, 3), (300, 16), (1000, 48), (2000, 16), (2049, 7)])
+def test_block_matvec(pkg, n, k):
+    rng = np.random.default_rng(n + k)
+    A = rng.standard_normal((n, n))
+    S = (A + A.T) / 2
+    Q = rng.standard_normal((n, k))
+    W = pkg.block_matvec(torch.tensor(S, dtype=torch.float32, device=DEV),
+                         torch.tensor(Q.T.copy(), dtype=torch.float32, device=DEV))
+    torch.cuda.synchronize()
+    Wg = W.double().cpu().numpy().T
+    ref = S.astype(np.float32).astype(np.float64) @ Q.astype(np.float32).astype(np.float64)
+    err = np.linalg.norm(Wg - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err <= 2e-6 * math.sqrt(n / 2000.0) + 1e-6
+
+
+@pytest.mark.parametrize("K", [2, 8, 33, 48, 64, 96, 128])
+def test_sym_eig(pkg, K):
+    rng = np.random.default_rng(K)
+    A = rng.standard_normal((K, K))
+    T = (A + A.T) / 2
+    theta, Y = pkg.sym_eig(torch.tensor(T, device=DEV))
+    torch.cuda.synchronize()
+    th = theta.cpu().numpy()
+    Yn = Y.double().cpu().numpy()
+    ref = np.sort(np.linalg.eigvalsh(T))[::-1]
+    nT = np.linalg.norm(T, 2)
+    assert np.max(np.abs(th - ref)) <= 2e-6 * nT
+    assert np.linalg.norm(T @ Yn - Yn * th) <= 1e-5 * nT * math.sqrt(K)
+    assert np.linalg.norm(Yn.T @ Yn - np.eye(K)) <= 1e-5 * math.sqrt(K)
+
+
+def _spectrum(n, npos, seed, gap=0.3):
+    rng = np.random.default_rng(seed)
+    pos = np.sort(rng.uniform(1.0, 10.0, npos))[::-1]
+    neg = -np.sort(rng.uniform(0.1, 40.0, n - npos))
+    lam = np.concatenate([pos, neg])
+    return lam
+
+
+@pytest.mark.parametrize("n,r,npos", [(50, 5, 10), (127, 8, 8), (129, 8, 20), (300, 8, 30), (777, 16, 24),
+                                      (1000, 32, 40), (2000, 8, 12), (2000, 16, 64)])
+def test_aproj_known_spectrum(pkg, n, r, npos):
+    lam = _spectrum(n, npos, seed=n + r)
+    # separate lambda_r from lambda_{r+1} by a relative gap so the truncation is unique
+    lam[:r] += 0.5
+    S, Q, lam = si.random_symmetric_with_spectrum(n, lam, seed=n)
+    order = np.argsort(-lam)
+    Pref = (Q[:, order[:r]] * np.maximum(lam[order[:r]], 0)) @ Q[:, order[:r]].T
+    P, V, lg, info = pkg.aproj(torch.tensor(S, dtype=torch.float32, device=DEV), r)
+    torch.cuda.synchronize()
+    err = np.linalg.norm(P.double().cpu().numpy() - Pref) / np.linalg.norm(Pref)
+    assert err <= 1e-5, (err, info.as_dict())
+    np.testing.assert_allclose(lg.cpu().numpy(), np.sort(lam)[::-1][:r], rtol=1e-5, atol=1e-5 * np.abs(lam).max())
+
+
+def test_aproj_negative_definite_gives_zero(pkg):
+    n = 300
+    lam = -np.linspace(0.5, 10, n)
+    S, _, _ = si.random_symmetric_with_spectrum(n, lam, seed=1)
+    P, V, lg, info = pkg.aproj(torch.tensor(S, dtype=torch.float32, device=DEV), 4)
+    torch.cuda.synchronize()
+    assert float(P.abs().max()) == 0.0
+    assert np.all(lg.cpu().numpy() < 0)
+
+
+# ---------------------------------------------------------------------------
+# one iteration of Alg. 2 from a shared iterate
+# ---------------------------------------------------------------------------
+
+def _shared_iterate(inst, r, iters):
+    prob = Problem.from_instance(inst)
+    res = oracle.solve(prob, mode="lr", tol=1e-12, rank_init=r, max_iter=iters, max_rank=r)
+    lam_x, U = np.linalg.eigh(res.X)
+    return prob, U[:, ::-1][:, :r].copy(), lam_x[::-1][:r].copy(), res.y_paper
+
+
+@pytest.mark.parametrize("kind,n,r", [("maxcut", 200, 4), ("maxcut", 90, 6), ("equi", 160, 8), ("sensor", 0, 8)])
+def test_one_iteration_matches_oracle(pkg, kind, n, r):
+    if kind == "maxcut":
+        inst = si.maxcut_er(n, 0.05, 3)
+    elif kind == "equi":
+        rng = np.random.default_rng(7)
+        ei, ej = si.erdos_renyi(n, 0.05, rng)
+        inst = si.equipartition(n, ei, ej, np.ones(ei.shape[0]))
+    else:
+        inst = si.sensor_network(140, 6, 0.3, seed=5)
+    prob, Vx, lx, yp = _shared_iterate(inst, r, 25)
+    sp, scale = normalize_rows(prob)
+    slv = pkg.Solver(rank_init=r, max_rank=r, lanczos_tol=1e-6, lanczos_max_cycles=30)
+    slv.set_instance(inst)
+    slv.set_iterate(Vx, lx, yp)
+    info = slv.iterate(1)
+    got = slv.get_primal_dual()
+    X0 = (Vx * np.maximum(lx, 0)) @ Vx.T
+    st = pd_iteration(sp, X0, -yp / scale, info.alpha, r)
+    ex = np.linalg.norm(got["X"] - st.X) / np.linalg.norm(st.X)
+    assert ex <= 1e-4, ex
+    y_ref = -st.y * scale
+    ey = np.linalg.norm(got["y"] - y_ref) / max(np.linalg.norm(y_ref), 1e-12)
+    assert ey <= 1e-4, ey
+    assert abs(info.eps_primal - st.eps_primal) <= 1e-3 * st.eps_primal + 1e-6
+    assert abs(info.eps_dual - st.eps_dual) <= 1e-3 * st.eps_dual + 1e-6
+    assert abs(info.lambda_r - st.lam_desc[r - 1]) <= 1e-4 * abs(st.lam_desc[0])
+    slv.close()
+
+
+# ---------------------------------------------------------------------------
+# full solves
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,graph", [(5, "K"), (6, "K"), (7, "C"), (64, "C"), (101, "C"), (16, "K")])
+def test_maxcut_closed_forms_small(pkg, n, graph):
+    ei, ej, w = si.complete_graph(n) if graph == "K" else si.cycle_graph(n)
+    inst = si.maxcut(n, ei, ej, w)
+    slv = pkg.Solver(tol=1e-6, rank_init=1, max_iter=200000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    if graph == "K":
+        want = -n * n / 4.0
+    else:
+        want = -(n / 2.0) * (1 + math.cos(math.pi / n)) if n % 2 else -float(n)
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - want) <= 1e-4 * abs(want)
+    slv.close()
+
+
+@pytest.mark.parametrize("n", [200, 257])
+def test_maxcut_cycle_closed_form_lanczos_path(pkg, n):
+    inst = si.maxcut(n, *si.cycle_graph(n))
+    slv = pkg.Solver(tol=1e-6, rank_init=2, max_iter=400000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    want = -(n / 2.0) * (1 + math.cos(math.pi / n)) if n % 2 else -float(n)
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - want) <= 1e-4 * abs(want)
+    slv.close()
+
+
+@pytest.mark.parametrize("n,p,seed", [(150, 0.05, 1), (300, 0.03, 2)])
+def test_maxcut_random_against_oracle(pkg, n, p, seed):
+    inst = si.maxcut_er(n, p, seed, weights="int5")
+    prob = Problem.from_instance(inst)
+    ref = oracle.solve(prob, mode="lr", tol=1e-6, rank_init=8)
+    slv = pkg.Solver(tol=1e-5, rank_init=8)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - ref.pobj) <= 1e-4 * abs(ref.pobj)
+    got = slv.get_primal_dual()
+    cert = oracle.certificates(prob, got["X"], -got["y"])
+    assert cert["primal_eq"] <= 1e-4 and cert["rel_gap"] <= 1e-4 and cert["dual_min_eig_rel"] >= -1e-4
+    slv.close()
+
+
+def test_equipartition_dense_row(pkg):
+    n = 240
+    ei, ej, w = si.cycle_graph(n)
+    inst = si.equipartition(n, ei, ej, w)
+    slv = pkg.Solver(tol=1e-6, rank_init=4, max_iter=400000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    want = (n / 2.0) * (1 - math.cos(2 * math.pi / n))
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - want) <= 1e-4 * abs(want) + 1e-5
+    slv.close()
+
+
+def test_inequality_rows(pkg):
+    """MaxCut plus inequality rows X_0j <= 0.3: multipliers >= 0, rows satisfied, certificate."""
+    n = 140
+    base = si.maxcut_er(n, 0.06, 4)
+    extra = 8
+    ptr = np.concatenate([base.A_rowptr, base.A_rowptr[-1] + np.arange(1, extra + 1)])
+    col = np.concatenate([base.A_col, si.svec_index(np.zeros(extra, int), np.arange(1, extra + 1))])
+    val = np.concatenate([base.A_val, np.full(extra, 0.5)])
+    rhs = np.concatenate([base.rhs, np.full(extra, 0.3)])
+    slv = pkg.Solver(tol=1e-5, rank_init=8)
+    slv.set_problem(n, n, ptr, col, val, rhs, C_idx=base.C_idx, C_val=base.C_val)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    got = slv.get_primal_dual()
+    prob = Problem.from_arrays(n, n, ptr, col, val, rhs, C_idx=base.C_idx, C_val=base.C_val)
+    ref = oracle.solve(prob, mode="lr", tol=1e-6, rank_init=8)
+    assert abs(info.primal_obj - ref.pobj) <= 1e-4 * abs(ref.pobj)
+    assert np.all(got["y"][n:] <= 1e-12)  # paper's sign: y_ineq <= 0
+    cert = oracle.certificates(prob, got["X"], -got["y"])
+    assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 1e-4
+    slv.close()
+
+
+# ---------------------------------------------------------------------------
+# the n = 2000 MaxCut workload (weights 1..5), certified at full size
+# ---------------------------------------------------------------------------
+
+def test_maxcut_2000_certified(pkg):
+    inst = si.config_maxcut_2000()
+    slv = pkg.Solver(tol=1e-4, rank_init=8, block_size=16)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    got = slv.get_primal_dual()
+    prob = Problem.from_instance(inst)
+    cert = oracle.certificates(prob, got["X"], -got["y"])
+    assert cert["primal_eq"] <= 1e-4
+    assert cert["rel_gap"] <= 2e-4
+    assert cert["dual_min_eig_rel"] >= -1e-3
+    assert cert["x_min_eig_rel"] >= -1e-6
+    slv.close()
+
+
+# ---------------------------------------------------------------------------
+# error handling at the boundary
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_rejected(pkg):
+    slv = pkg.Solver()
+    with pytest.raises(pkg.ProxSDPError) as e:
+        slv.set_problem(4, 1, [0, 1], [99], [1.0], [1.0], C_idx=[0], C_val=[1.0])  # svec index out of range
+    assert e.value.code == -1
+    with pytest.raises(pkg.ProxSDPError) as e:
+        slv.set_problem(4, 1, [0, 2, 1], [0, 2], [1.0, 1.0], [1.0, 1.0], C_idx=[0], C_val=[1.0])  # bad rowptr
+    assert e.value.code == -1
+    with pytest.raises(pkg.ProxSDPError) as e:
+        slv.set_problem(4, 1, [0, 1], [0], [float("nan")], [1.0], C_idx=[0], C_val=[1.0])
+    assert e.value.code == -1
+    with pytest.raises(pkg.ProxSDPError) as e:
+        slv.solve()  # no problem loaded
+    assert e.value.code == -4
+    slv.close()
