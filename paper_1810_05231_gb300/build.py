@@ -42,8 +42,26 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _check_stamp():
+    """Objects built on another host architecture are discarded."""
+    import platform
+
+    stamp = os.path.join(BUILD, "HOST")
+    want = platform.machine()
+    have = open(stamp).read().strip() if os.path.exists(stamp) else None
+    if have != want:
+        for f in os.listdir(BUILD):
+            if f.endswith(".o"):
+                os.remove(os.path.join(BUILD, f))
+        if os.path.exists(LIB):
+            os.remove(LIB)
+        with open(stamp, "w") as fh:
+            fh.write(want + "\n")
+
+
 def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    _check_stamp()
     cc = nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(INCLUDE, "proxsdp_gpu.h"))
