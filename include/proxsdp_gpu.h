@@ -88,7 +88,7 @@ typedef struct {
   int precision;          /* PROXSDP_PREC_FP32                                           [0]   */
   int normalize_rows;     /* scale each (A_i, rhs_i) to ||A_i||_F = 1                    [1]   */
   uint64_t seed;          /* Lanczos start block                                         [1]   */
-  int max_rank;           /* cap on the target rank                                      [128] */
+  int max_rank;           /* cap on the target rank (Lanczos path: <= 60)                [60]  */
   int lanczos_steps;      /* block Krylov steps per restart cycle (0: automatic)         [0]   */
   int lanczos_max_cycles; /* restart cycles per projection                               [8]   */
   double lanczos_tol;     /* Ritz residual tolerance relative to |theta_1| (0: adaptive) [0]   */
@@ -116,6 +116,7 @@ typedef struct {
   int64_t lanczos_unconverged; /* projections that hit lanczos_max_cycles */
   double alpha;              /* step size used */
   double norm_M;             /* ||M||_2 of the row-scaled operator */
+  int64_t kernel_launches;   /* library kernels executed by the iterations of this call sequence */
 } proxsdp_gpu_info;
 
 /* Fill *s with the defaults above. */

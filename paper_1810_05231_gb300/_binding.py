@@ -89,6 +89,7 @@ class Info(ctypes.Structure):
         ("lanczos_unconverged", ctypes.c_int64),
         ("alpha", ctypes.c_double),
         ("norm_M", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -327,67 +327,62 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric eigensolver: parallel cyclic Jacobi in one CTA
+// Symmetric eigensolver: parallel cyclic Jacobi in one CTA + refinement
 // ---------------------------------------------------------------------------
-// Round-robin ordering: in round s (0..K-2) position K-1 meets s and, for
-// t = 1..K/2-1, (s+t) mod (K-1) meets (s-t) mod (K-1); every pair meets once
-// per sweep and the K/2 rotations of a round act on disjoint index pairs.
-// Each rotation J (c, s in the (p,q) plane) is chosen to zero A_pq
-// (tan 2 theta = 2 A_pq / (A_qq - A_pp)); A <- J^T A J, V <- V J.
-template <typename T>
-struct JacobiTraits;
-template <>
-struct JacobiTraits<float> {
-  static constexpr double tol2 = 1e-14;
-};
-template <>
-struct JacobiTraits<double> {
-  static constexpr double tol2 = 1e-28;
-};
+// (1) Cyclic Jacobi in FP32.  Round-robin ordering: in round s (0..K-2)
+//     position K-1 meets s and, for t = 1..K/2-1, (s+t) mod (K-1) meets
+//     (s-t) mod (K-1); the K/2 rotations of a round act on disjoint pairs.
+//     Each rotation J (c, s in the (p,q) plane) zeroes A_pq
+//     (tan 2 theta = 2 A_pq / (A_qq - A_pp)); A <- J^T A J, V <- V J.
+//     Pairs with |A_pq| below 1e-7 sqrt(|A_pp A_qq|) are not rotated.  Sweeps
+//     stop when off(A) <= 1e-6 ||A||_F.
+// (2) One refinement step for the `nout` wanted eigenvectors (Ogita & Aishima,
+//     "Iterative refinement for symmetric eigenvalue decomposition", 2018):
+//     with Y the Jacobi vectors, S = Y^T T Y and R = I - Y^T Y accumulated in
+//     FP32 pairs against the FP64 input T, lambda_j = S_jj / (1 - R_jj) and
+//     y_j <- y_j + sum_i y_i E_ij,  E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
+//     (E_ij = R_ij / 2 for i = j or nearly equal eigenvalues).  The refined
+//     eigenvalues are FP64-accurate; the vectors are FP32-rounded.
+constexpr int JB = 32;  // wanted columns refined per pass
 
-template <typename T>
 __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, int K, int Kp,
-                                                double* __restrict__ theta, T* __restrict__ Yout,
+                                                double* __restrict__ theta, float* __restrict__ Yout,
                                                 int ldy, int nout, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ float smj[];
   const int ld = Kp + 1;
-  T* A = reinterpret_cast<T*>(smraw);
-  T* V = A + (size_t)Kp * ld;
-  T* cs = V + (size_t)Kp * ld;      // Kp/2 cosines
-  T* sn = cs + Kp / 2;              // Kp/2 sines
-  int* pp = reinterpret_cast<int*>(sn + Kp / 2);
+  float* A = smj;                      // Kp x (Kp+1)
+  float* V = A + (size_t)Kp * ld;      // Kp x (Kp+1)
+  float* cs = V + (size_t)Kp * ld;     // Kp/2
+  float* sn = cs + Kp / 2;             // Kp/2
+  float* dg = sn + Kp / 2;             // Kp: eigenvalue estimates
+  int* pp = reinterpret_cast<int*>(dg + Kp);
   int* qq = pp + Kp / 2;
-  double* red = reinterpret_cast<double*>(qq + Kp / 2 + 2);  // 2 * 32 doubles (8-aligned below)
-  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  int* rank = qq + Kp / 2;             // Kp
+  int* wanted = rank + Kp;             // JB
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wanted + JB) + 7) & ~uintptr_t(7));
+  double* lamj = red + 64;             // JB
   __shared__ int s_stop;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int half = Kp / 2;
 
-  // load (symmetrised); padded indices get an isolated, very negative diagonal
-  double dmin = 0.0;
   for (int idx = tid; idx < Kp * Kp; idx += nth) {
     int i = idx / Kp, j = idx % Kp;
     double v = 0.0;
     if (i < K && j < K) v = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
-    A[i * ld + j] = (T)v;
-    V[i * ld + j] = (T)(i == j ? 1.0 : 0.0);
+    A[i * ld + j] = (float)v;
+    V[i * ld + j] = (i == j) ? 1.f : 0.f;
   }
   __syncthreads();
-  if (Kp > K) {
-    if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < K; ++i) s += fabs((double)A[i * ld + i]);
-      for (int i = 0; i < K; ++i)
-        for (int j = 0; j < K; ++j) s = fmax(s, fabs((double)A[i * ld + j]));
-      dmin = -4.0 * (s + 1.0) * K;
-      for (int i = K; i < Kp; ++i) A[i * ld + i] = (T)dmin;
-    }
-    __syncthreads();
+  if (Kp > K && tid == 0) {  // isolated padding index, below every eigenvalue
+    float s = 0.f;
+    for (int i = 0; i < K; ++i)
+      for (int j = 0; j < K; ++j) s = fmaxf(s, fabsf(A[i * ld + j]));
+    A[K * ld + K] = -4.f * (s + 1.f) * (float)K;
   }
+  __syncthreads();
 
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    // convergence test: off(A)^2 <= tol2 * ||A||_F^2
+  for (int sweep = 0; sweep < 15; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = tid; idx < K * K; idx += nth) {
       int i = idx / K, j = idx % K;
@@ -410,7 +405,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
         o2 += red[k];
         t2 += red[32 + k];
       }
-      s_stop = (o2 <= JacobiTraits<T>::tol2 * t2) || (t2 == 0.0);
+      s_stop = (o2 <= 1e-12 * t2) || (t2 == 0.0);
     }
     __syncthreads();
     if (s_stop) break;
@@ -429,15 +424,15 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
           p = q;
           q = t;
         }
-        T apq = A[p * ld + q];
-        T c = (T)1, s = (T)0;
-        if (apq != (T)0) {
-          T app = A[p * ld + p], aqq = A[q * ld + q];
-          T tau = (aqq - app) / ((T)2 * apq);
-          T t;
-          if (fabs((double)tau) > 1e15) t = (T)0.5 / tau;
-          else t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
-          c = (T)1 / sqrt((T)1 + t * t);
+        float apq = A[p * ld + q];
+        float app = A[p * ld + p], aqq = A[q * ld + q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
+          float tau = (aqq - app) / (2.f * apq);
+          float t;
+          if (fabsf(tau) > 1e15f) t = 0.5f / tau;
+          else t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = 1.f / sqrtf(1.f + t * t);
           s = t * c;
         }
         cs[tid] = c;
@@ -446,76 +441,140 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
         qq[tid] = q;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int idx = tid; idx < half * Kp; idx += nth) {
+      for (int idx = tid; idx < half * Kp; idx += nth) {  // rows: A <- J^T A
         int t = idx / Kp, j = idx % Kp;
+        float c = cs[t], s = sn[t];
+        if (s == 0.f) continue;
         int p = pp[t], q = qq[t];
-        T c = cs[t], s = sn[t];
-        T ap = A[p * ld + j], aq = A[q * ld + j];
+        float ap = A[p * ld + j], aq = A[q * ld + j];
         A[p * ld + j] = c * ap - s * aq;
         A[q * ld + j] = s * ap + c * aq;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int idx = tid; idx < half * Kp; idx += nth) {
+      for (int idx = tid; idx < half * Kp; idx += nth) {  // columns: A <- A J, V <- V J
         int t = idx / Kp, i = idx % Kp;
+        float c = cs[t], s = sn[t];
+        if (s == 0.f) continue;
         int p = pp[t], q = qq[t];
-        T c = cs[t], s = sn[t];
-        T ap = A[i * ld + p], aq = A[i * ld + q];
+        float ap = A[i * ld + p], aq = A[i * ld + q];
         A[i * ld + p] = c * ap - s * aq;
         A[i * ld + q] = s * ap + c * aq;
-        T vp = V[i * ld + p], vq = V[i * ld + q];
+        float vp = V[i * ld + p], vq = V[i * ld + q];
         V[i * ld + p] = c * vp - s * vq;
         V[i * ld + q] = s * vp + c * vq;
       }
       __syncthreads();
-      if (tid < half) {  // the rotation annihilates A_pq exactly
-        A[pp[tid] * ld + qq[tid]] = (T)0;
-        A[qq[tid] * ld + pp[tid]] = (T)0;
+      if (tid < half) {
+        A[pp[tid] * ld + qq[tid]] = 0.f;
+        A[qq[tid] * ld + pp[tid]] = 0.f;
       }
       __syncthreads();
     }
   }
-  // sort eigenvalues descending (rank by comparison, ties by index)
+  // eigenvalue estimates and their descending order (ties by index)
+  for (int i = tid; i < Kp; i += nth) dg[i] = A[i * ld + i];
+  __syncthreads();
+  float scale = 0.f;
+  for (int i = 0; i < K; ++i) scale = fmaxf(scale, fabsf(dg[i]));
+  const float delta = 1e-4f * fmaxf(scale, 1e-30f);  // eigenvalues closer than this form a cluster
   for (int i = tid; i < K; i += nth) {
-    double di = (double)A[i * ld + i];
-    int rank = 0;
+    float di = dg[i];
+    int rk = 0;
     for (int j = 0; j < K; ++j) {
-      double dj = (double)A[j * ld + j];
-      rank += (dj > di) || (dj == di && j < i);
+      float dj = dg[j];
+      rk += (dj > di) || (dj == di && j < i);
     }
-    if (rank < nout) {
-      theta[rank] = di;
-      for (int row = 0; row < K; ++row) Yout[(size_t)rank * ldy + row] = V[row * ld + i];
+    rank[i] = rk;
+  }
+  __syncthreads();
+  // A is free now: per pass, Ph | Pl | Sm | Rm  (each Kp x jb floats, 4 Kp jb <= Kp (Kp+1))
+  const int jb = max(1, min(JB, (Kp + 1) / 4));
+  float* Ph = A;
+  float* Pl = Ph + Kp * jb;
+  float* Sm = Pl + Kp * jb;
+  float* Rm = Sm + Kp * jb;
+  for (int j0 = 0; j0 < nout; j0 += jb) {
+    const int nb = min(jb, nout - j0);
+    for (int i = tid; i < K; i += nth) {
+      int rk = rank[i];
+      if (rk >= j0 && rk < j0 + nb) wanted[rk - j0] = i;
     }
+    __syncthreads();
+    // P = T Y_wanted  (FP32-pair accumulation, T split into hi + lo)
+    for (int o = tid; o < K * nb; o += nth) {
+      int k = o / nb, jj = o % nb;
+      const int j = wanted[jj];
+      DF acc;
+      for (int l = 0; l < K; ++l) {
+        double t = 0.5 * (Tin[k * K + l] + Tin[l * K + k]);
+        float hi = (float)t;
+        float lo = (float)(t - (double)hi);
+        float y = V[l * ld + j];
+        acc.fma_acc(hi, y);
+        acc.fma_acc(lo, y);
+      }
+      Ph[k * jb + jj] = acc.hi;
+      Pl[k * jb + jj] = acc.lo;
+    }
+    __syncthreads();
+    // S = Y^T P, R = I - Y^T Y_wanted
+    for (int o = tid; o < K * nb; o += nth) {
+      int i = o / nb, jj = o % nb;
+      const int j = wanted[jj];
+      DF s_acc, r_acc;
+      for (int k = 0; k < K; ++k) {
+        float yi = V[k * ld + i];
+        s_acc.fma_acc(yi, Ph[k * jb + jj]);
+        s_acc.fma_acc(yi, Pl[k * jb + jj]);
+        r_acc.fma_acc(yi, V[k * ld + j]);
+      }
+      double rv = (i == j ? 1.0 : 0.0) - r_acc.value();
+      if (i == j) lamj[jj] = s_acc.value() / (1.0 - rv);
+      Sm[i * jb + jj] = (float)s_acc.value();
+      Rm[i * jb + jj] = (float)rv;
+    }
+    __syncthreads();
+    // E (in place of S)
+    for (int o = tid; o < K * nb; o += nth) {
+      int i = o / nb, jj = o % nb;
+      const int j = wanted[jj];
+      float r = Rm[i * jb + jj];
+      float e;
+      float lj = (float)lamj[jj];
+      float gap = lj - dg[i];
+      if (i == j || fabsf(gap) <= delta) e = 0.5f * r;
+      else e = (Sm[i * jb + jj] + lj * r) / gap;
+      Sm[i * jb + jj] = e;
+    }
+    __syncthreads();
+    // y_j <- y_j + Y E_j
+    for (int o = tid; o < K * nb; o += nth) {
+      int row = o / nb, jj = o % nb;
+      const int j = wanted[jj];
+      float acc = V[row * ld + j];
+      for (int i = 0; i < K; ++i) acc = fmaf(V[row * ld + i], Sm[i * jb + jj], acc);
+      Yout[(size_t)(j0 + jj) * ldy + row] = acc;
+    }
+    for (int jj = tid; jj < nb; jj += nth) theta[j0 + jj] = lamj[jj];
+    __syncthreads();
   }
 }
 
-template <typename T>
 static size_t jacobi_smem(int Kp) {
   size_t ld = Kp + 1;
-  return (2 * (size_t)Kp * ld + (size_t)Kp) * sizeof(T) + ((size_t)Kp + 2) * sizeof(int) + 8 +
-         64 * sizeof(double);
+  size_t f = 2 * (size_t)Kp * ld + (size_t)Kp + (size_t)Kp;  // A, V, cs+sn, dg
+  size_t ints = (size_t)Kp + (size_t)Kp + JB;                // pp+qq, rank, wanted
+  return f * sizeof(float) + ints * sizeof(int) + 8 + (64 + JB) * sizeof(double);
 }
 
 void init_lanczos_attributes() {
-  cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)jacobi_smem<float>(kMaxK));
-  cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)jacobi_smem<double>(kFullEigMax - 24));
+  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxK));
 }
 
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
                     const int* skip, cudaStream_t st) {
   int Kp = (K + 1) & ~1;
-  size_t sm = jacobi_smem<float>(Kp);
-  k_jacobi<float><<<1, 512, sm, st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
-}
-
-void launch_sym_eig_f64(const double* T, int K, double* theta, double* Y, int ldy, cudaStream_t st) {
-  int Kp = (K + 1) & ~1;
-  size_t sm = jacobi_smem<double>(Kp);
-  k_jacobi<double><<<1, 512, sm, st>>>(T, K, Kp, theta, Y, ldy, K, nullptr);
+  k_jacobi<<<1, 512, jacobi_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
 }
 
 }  // namespace psdp

@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     ctl->lz_cycle += 1;
     ctl->lz_cycles_total += 1;
     ctl->matvecs += s_steps;
+    ctl->launches += 12LL * s_steps + 3;  // copy + 10 orthogonalisation kernels + product per step; Gram, Jacobi, Ritz
     bool ok = worst <= ctl->lz_tol || !(worst == worst);
     if (ok || ctl->lz_cycle >= ctl->max_cycles) {
       if (!ok) ctl->lz_unconverged += 1;
@@ -373,6 +374,7 @@ __global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, cons
   ctl->lam_r = lam_r;
   ctl->normX = normX;
   ctl->matvecs += 1;  // warm-start product of the next iteration
+  ctl->launches += ctl->full_eig_path ? 10 : 9;  // per-iteration kernels outside the restart cycles
   const double comb = eps_p + eps_d;
   const int win = ctl->window;
   const double old = ctl->hist[it % win];

@@ -51,10 +51,12 @@ struct Ctl {
   int max_rank;
   int max_cycles;
   int fixed_rank;    // 1: never change r (building-block use)
-  int pad0, pad1;
+  int full_eig_path; // projection by dense Jacobi (n <= 128 or Alg. 1)
+  int pad1;
   long long matvecs;
   long long lz_cycles_total;
   long long lz_unconverged;
+  long long launches;   // kernels launched by the iteration (graph nodes executed)
   double tol, eps_lambda, lz_tol_fixed, lz_tol;
   double eps_p, eps_d, rel_p, rel_d, rel_gap, pobj, dobj, lam_r, normX, lz_res;
   double red_dual[kRedSlots];
@@ -145,7 +147,6 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
                        unsigned long long seed, const int* skip, cudaStream_t st);
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
                     const int* skip, cudaStream_t st);
-void launch_sym_eig_f64(const double* T, int K, double* theta, double* Y, int ldy, cudaStream_t st);
 void init_lanczos_attributes();
 
 // ---------------------------------------------------------------------------

@@ -346,6 +346,7 @@ int Solver::init_iterate_zero() {
   c.K = K;
   c.status = ST_RUNNING;
   c.full_eig = set.full_eig ? 1 : 0;
+  c.full_eig_path = (n <= kFullEigMax || set.full_eig) ? 1 : 0;
   c.window = std::max(1, std::min(set.window, kMaxWindow));
   c.max_rank = set.full_eig ? n : std::min(set.max_rank, n);
   c.max_cycles = std::max(1, set.lanczos_max_cycles);
@@ -483,6 +484,7 @@ int Solver::run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info
     info->lanczos_unconverged = c.lz_unconverged;
     info->alpha = hp.alpha;
     info->norm_M = hp.normM;
+    info->kernel_launches = c.launches;
   }
   return PROXSDP_OK;
 }
