@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
   int* wanted = rank + Kp;             // JB
   double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wanted + JB) + 7) & ~uintptr_t(7));
   double* lamj = red + 64;             // JB
+  float* scr = reinterpret_cast<float*>(lamj + JB);  // 4 * Kp * JB refinement scratch
   __shared__ int s_stop;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int half = Kp / 2;
@@ -487,9 +488,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
     rank[i] = rk;
   }
   __syncthreads();
-  // A is free now: per pass, Ph | Pl | Sm | Rm  (each Kp x jb floats, 4 Kp jb <= Kp (Kp+1))
-  const int jb = max(1, min(JB, (Kp + 1) / 4));
-  float* Ph = A;
+  // refinement scratch, per pass: Ph | Pl | Sm | Rm  (each Kp x jb floats)
+  const int jb = JB;
+  float* Ph = scr;
   float* Pl = Ph + Kp * jb;
   float* Sm = Pl + Kp * jb;
   float* Rm = Sm + Kp * jb;
@@ -564,7 +565,8 @@ static size_t jacobi_smem(int Kp) {
   size_t ld = Kp + 1;
   size_t f = 2 * (size_t)Kp * ld + (size_t)Kp + (size_t)Kp;  // A, V, cs+sn, dg
   size_t ints = (size_t)Kp + (size_t)Kp + JB;                // pp+qq, rank, wanted
-  return f * sizeof(float) + ints * sizeof(int) + 8 + (64 + JB) * sizeof(double);
+  return f * sizeof(float) + ints * sizeof(int) + 8 + (64 + JB) * sizeof(double) +
+         4 * (size_t)Kp * JB * sizeof(float);
 }
 
 void init_lanczos_attributes() {

@@ -537,6 +537,22 @@ __global__ void k_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K
   if (k_change >= 0) ctl->k_change = k_change;
 }
 
+// debugging aid: count non-finite entries of a buffer
+template <typename T>
+__global__ void k_count_nonfinite(const T* p, size_t count, unsigned* out) {
+  unsigned c = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    c += !isfinite((double)p[i]);
+  if (c) atomicAdd(out, c);
+}
+
+void launch_count_nonfinite_f(const float* p, size_t count, unsigned* out, cudaStream_t st) {
+  k_count_nonfinite<float><<<64, 256, 0, st>>>(p, count, out);
+}
+void launch_count_nonfinite_d(const double* p, size_t count, unsigned* out, cudaStream_t st) {
+  k_count_nonfinite<double><<<64, 256, 0, st>>>(p, count, out);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------

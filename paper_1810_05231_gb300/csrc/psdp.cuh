@@ -171,5 +171,7 @@ void launch_iter_begin(const DevWork& wk, cudaGraphConditionalHandle inner, int 
 void launch_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change,
                     cudaStream_t st);
 void init_pdhg_attributes();
+void launch_count_nonfinite_f(const float* p, size_t count, unsigned* out, cudaStream_t st);
+void launch_count_nonfinite_d(const double* p, size_t count, unsigned* out, cudaStream_t st);
 
 }  // namespace psdp

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "solver.h"
@@ -27,6 +29,48 @@ namespace psdp {
     cudaError_t e_ = (call);                                                  \
     if (e_ != cudaSuccess) return fail(PROXSDP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
+
+// Debugging aid (environment variable PSDP_DEBUG=1, direct launches only):
+// after every kernel, synchronise and report the first buffer that holds a
+// non-finite value, with the name of the kernel that ran last.
+static bool g_debug = getenv("PSDP_DEBUG") != nullptr;
+static bool g_debug_reported = false;
+static unsigned* g_debug_cnt = nullptr;
+static int g_debug_n = 0;
+
+static void dbg(const DevWork& wk, const char* tag, cudaStream_t st) {
+  if (!g_debug || g_debug_reported) return;
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  if (!g_debug_cnt) cudaMallocManaged(&g_debug_cnt, 16 * sizeof(unsigned));
+  const int n = g_debug_n;
+  struct B {
+    const char* name;
+    const void* p;
+    size_t count;
+    bool dbl;
+  } bufs[] = {{"S", wk.S, (size_t)n * wk.lds, false}, {"Q", wk.Q, (size_t)wk.ldq * kMaxK, false},
+              {"W", wk.W, (size_t)wk.ldq * kMaxK, false}, {"Vrm0", wk.Vrm[0], (size_t)n * kMaxR, false},
+              {"Vrm1", wk.Vrm[1], (size_t)n * kMaxR, false}, {"lam0", wk.lam[0], kMaxR, true},
+              {"lam1", wk.lam[1], kMaxR, true}, {"H", wk.H, (size_t)kMaxK * kMaxK, true},
+              {"Y", wk.Y, (size_t)kMaxK * kMaxK, false}, {"theta", wk.theta, kMaxK, true},
+              {"Hf", wk.Hf, (size_t)kMaxW * kMaxW, false}};
+  const int nb = sizeof(bufs) / sizeof(bufs[0]);
+  cudaStreamSynchronize(st);
+  for (int b = 0; b < nb; ++b) g_debug_cnt[b] = 0;
+  for (int b = 0; b < nb; ++b) {
+    if (!bufs[b].p) continue;
+    if (bufs[b].dbl) launch_count_nonfinite_d((const double*)bufs[b].p, bufs[b].count, g_debug_cnt + b, st);
+    else launch_count_nonfinite_f((const float*)bufs[b].p, bufs[b].count, g_debug_cnt + b, st);
+  }
+  cudaStreamSynchronize(st);
+  for (int b = 0; b < nb; ++b) {
+    if (g_debug_cnt[b]) {
+      fprintf(stderr, "[psdp debug] after %s: %u non-finite values in %s\n", tag, g_debug_cnt[b], bufs[b].name);
+      g_debug_reported = true;
+    }
+  }
+}
 
 void init_kernel_attributes() {
   static bool done = false;
@@ -179,7 +223,7 @@ void Solver::dims(int rr, int& w, int& K, int& s) const {
   w = ((rr + g + b - 1) / b) * b;
   w = std::min(w, kMaxW);
   if (set.lanczos_steps > 0) s = set.lanczos_steps;
-  else s = std::max(1, 64 / w - 1);
+  else s = std::max(1, k_target / w - 1);
   while ((s + 1) * w > kMaxK && s > 1) --s;
   K = (s + 1) * w;
 }
@@ -200,12 +244,17 @@ static void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long 
   for (int pass = 0; pass < 2; ++pass) {
     if (c0 > 0) {
       launch_gram(wk.Q, wk.ldq, c0, Z, wk.ldq, w, n, wk.H, wk.part, cnt, skip, st);
+      dbg(wk, "orth gram QtZ", st);
       launch_block_update(Z, wk.ldq, w, wk.Q, wk.ldq, c0, wk.H, n, skip, st);
+      dbg(wk, "orth update", st);
     }
     launch_gram(Z, wk.ldq, w, Z, wk.ldq, w, n, wk.H, wk.part, cnt, skip, st);
+    dbg(wk, "orth gram ZtZ", st);
     launch_chol_inv(wk.H, w, wk.Hf, wk.flags, skip, st);
+    dbg(wk, "orth chol", st);
     launch_apply_rinv(Z, wk.ldq, w, wk.Hf, wk.flags, n, seed * 131ULL + (unsigned long long)(pass * 7 + c0),
                       skip, st);
+    dbg(wk, "orth apply", st);
   }
 }
 
@@ -219,10 +268,14 @@ static void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
     enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st);
     launch_block_matvec(wk.S, wk.lds, n, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
                         wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st);
+    dbg(wk, "cycle matvec", st);
   }
   launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
+  dbg(wk, "rr gram T", st);
   launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st);
+  dbg(wk, "rr jacobi", st);
   launch_ritz(wk, n, K, w, r, s, cond, use_cond, st);
+  dbg(wk, "ritz", st);
 }
 
 // Enqueue one iteration on `st` (direct launches or inside a capture).
@@ -235,7 +288,9 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
     launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, st);
     launch_full_eig_factors(wk, n, st);
   } else {
+    g_debug_n = n;
     launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st);
+    dbg(wk, "warm matvec", st);
     if (in_graph) {
       launch_iter_begin(wk, inner, 1, st);
       cudaStreamCaptureStatus cs;
@@ -261,15 +316,19 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
         enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed + 977ULL * (unsigned long long)c, inner, 0, st);
     }
   }
+  dbg(wk, "projection", st);
   launch_save_factor(wk, Vcm, n, k.full ? n : k.w, st);
   launch_mx(pb, wk, k.r, st);
   launch_dual(pb, wk, k.r, st);
   launch_dvals(pb, wk, st);
+  dbg(wk, "mx/dual/dvals", st);
   const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
   launch_gram(Vcm, wk.ldq, 2 * kMaxR, Vcm, wk.ldq, 2 * kMaxR, n, Hx, wk.part,
               wk.counters + CNT_CTL * 512, nullptr, st, act, kMaxR);
   launch_control(pb, wk, Hx, outer, use, st);
+  dbg(wk, "control", st);
   launch_rebuild(pb, wk, k.r, 0, st);
+  dbg(wk, "rebuild", st);
   CK(cudaGetLastError());
   return PROXSDP_OK;
 }
@@ -574,6 +633,7 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
                  const proxsdp_gpu_settings& set, cudaStream_t st_in, proxsdp_gpu_info* info,
                  std::string& err) {
   Solver sv;
+  sv.k_target = kMaxK;  // cold start: the largest Rayleigh-Ritz basis
   sv.set = set;
   sv.set.full_eig = 0;
   sv.seed = set.seed ? set.seed : 1;
