@@ -547,7 +547,7 @@ int proxsdp_gpu_aproj(const float* S, int64_t n, int64_t lds, int r, float* P, i
   if (settings) s = *settings;
   else {
     proxsdp_gpu_settings_default(&s);
-    s.lanczos_max_cycles = 30;
+    s.lanczos_max_cycles = 100;
     s.lanczos_tol = 1e-6;
   }
   std::string err;

@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
   __syncthreads();
   float scale = 0.f;
   for (int i = 0; i < K; ++i) scale = fmaxf(scale, fabsf(dg[i]));
-  const float delta = 1e-4f * fmaxf(scale, 1e-30f);  // eigenvalues closer than this form a cluster
+  const float delta = 1e-3f * fmaxf(scale, 1e-30f);  // eigenvalues closer than this form a cluster
   for (int i = tid; i < K; i += nth) {
     float di = dg[i];
     int rk = 0;
@@ -558,6 +558,31 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
     }
     for (int jj = tid; jj < nb; jj += nth) theta[j0 + jj] = lamj[jj];
     __syncthreads();
+  }
+  // Symmetric orthonormality correction of the refined vectors (the first-
+  // order refinement leaves O(E^2) non-orthogonality): with G = Y^T Y from
+  // FP32-pair sums, Y <- Y (3I - G) / 2, which maps G to I + O((G - I)^2).
+  // A (now free) holds I - G, V (now free) the corrected columns.
+  for (int o = tid; o < nout * nout; o += nth) {
+    int i = o / nout, j = o % nout;
+    if (j < i) continue;
+    DF g;
+    for (int k = 0; k < K; ++k) g.fma_acc(Yout[(size_t)i * ldy + k], Yout[(size_t)j * ldy + k]);
+    float v = (float)((i == j ? 1.0 : 0.0) - g.value());
+    A[i * nout + j] = v;
+    A[j * nout + i] = v;
+  }
+  __syncthreads();
+  for (int o = tid; o < K * nout; o += nth) {
+    int row = o / nout, j = o % nout;
+    float corr = 0.f;
+    for (int i = 0; i < nout; ++i) corr = fmaf(Yout[(size_t)i * ldy + row], A[i * nout + j], corr);
+    V[row * ld + j] = Yout[(size_t)j * ldy + row] + 0.5f * corr;
+  }
+  __syncthreads();
+  for (int o = tid; o < K * nout; o += nth) {
+    int row = o / nout, j = o % nout;
+    Yout[(size_t)j * ldy + row] = V[row * ld + j];
   }
 }
 

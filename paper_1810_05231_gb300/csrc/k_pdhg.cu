@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, cons
   ctl->lam_r = lam_r;
   ctl->normX = normX;
   ctl->matvecs += 1;  // warm-start product of the next iteration
-  ctl->launches += ctl->full_eig_path ? 10 : 9;  // per-iteration kernels outside the restart cycles
+  ctl->launches += ctl->full_eig_path ? 10 : 12;  // per-iteration kernels outside the restart cycles
   const double comb = eps_p + eps_d;
   const int win = ctl->window;
   const double old = ctl->hist[it % win];
@@ -383,7 +383,8 @@ __global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, cons
   if (ctl->lz_tol_fixed > 0.0) ctl->lz_tol = ctl->lz_tol_fixed;
   else ctl->lz_tol = fmin(1e-3, fmax(2e-6, 0.05 * fmax(rel_p, rel_d)));
   int status = ST_RUNNING;
-  if (!(comb == comb) || !(pobj == pobj)) {
+  if (!(ep2 == ep2) || !(ed2 == ed2) || !(pobj == pobj) || !(dobj == dobj) || !(x1 == x1) ||
+      !(lam_r == lam_r) || fabs(pobj) > 1e300) {
     status = ST_NUMERIC;
   } else {
     const bool conv = fmax(rel_p, fmax(rel_d, rel_gap)) <= ctl->tol;

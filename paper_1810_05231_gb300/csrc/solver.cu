@@ -258,6 +258,15 @@ static void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long 
   }
 }
 
+// One Cholesky-QR pass on Q[:, c0:c0+w] (re-orthonormalises the kept Ritz block).
+static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned long long seed, cudaStream_t st) {
+  float* Z = wk.Q + (size_t)c0 * wk.ldq;
+  unsigned* cnt = wk.counters + CNT_GRAM * 512;
+  launch_gram(Z, wk.ldq, w, Z, wk.ldq, w, n, wk.H, wk.part, cnt, nullptr, st);
+  launch_chol_inv(wk.H, w, wk.Hf, wk.flags, nullptr, st);
+  launch_apply_rinv(Z, wk.ldq, w, wk.Hf, wk.flags, n, seed, nullptr, st);
+}
+
 static void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
                           unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
                           cudaStream_t st) {
@@ -289,6 +298,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
     launch_full_eig_factors(wk, n, st);
   } else {
     g_debug_n = n;
+    enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
     launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st);
     dbg(wk, "warm matvec", st);
     if (in_graph) {

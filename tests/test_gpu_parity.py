@@ -159,7 +159,7 @@ def test_one_iteration_matches_oracle(pkg, kind, n, r):
 def test_maxcut_closed_forms_small(pkg, n, graph):
     ei, ej, w = si.complete_graph(n) if graph == "K" else si.cycle_graph(n)
     inst = si.maxcut(n, ei, ej, w)
-    slv = pkg.Solver(tol=1e-6, rank_init=1, max_iter=200000)
+    slv = pkg.Solver(tol=1e-6, rank_init=1, max_iter=100000)
     slv.set_instance(inst)
     info = slv.solve()
     if graph == "K":
@@ -174,7 +174,7 @@ def test_maxcut_closed_forms_small(pkg, n, graph):
 @pytest.mark.parametrize("n", [200, 257])
 def test_maxcut_cycle_closed_form_lanczos_path(pkg, n):
     inst = si.maxcut(n, *si.cycle_graph(n))
-    slv = pkg.Solver(tol=1e-6, rank_init=2, max_iter=400000)
+    slv = pkg.Solver(tol=1e-5, rank_init=2, max_iter=100000)
     slv.set_instance(inst)
     info = slv.solve()
     want = -(n / 2.0) * (1 + math.cos(math.pi / n)) if n % 2 else -float(n)
@@ -203,7 +203,7 @@ def test_equipartition_dense_row(pkg):
     n = 240
     ei, ej, w = si.cycle_graph(n)
     inst = si.equipartition(n, ei, ej, w)
-    slv = pkg.Solver(tol=1e-6, rank_init=4, max_iter=400000)
+    slv = pkg.Solver(tol=1e-5, rank_init=4, max_iter=100000)
     slv.set_instance(inst)
     info = slv.solve()
     want = (n / 2.0) * (1 - math.cos(2 * math.pi / n))
