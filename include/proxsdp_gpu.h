@@ -141,6 +141,19 @@ int proxsdp_gpu_set_problem(proxsdp_gpu_t h, int64_t n, const double* C_dense, i
                             int64_t m_eq, const int64_t* A_rowptr, const int64_t* A_col,
                             const double* A_val, const double* rhs);
 
+/* Host-only analysis of a problem (no device needed): validates the data
+ * exactly as set_problem does and reports the row-scaled operator norm
+ * ||M||_2 (power iteration on the Gram operator v -> M(M*(v))), the step
+ * alpha = alpha_frac/||M||_2 (Sec. 2.2 requires alpha < 1/||M||_2), the
+ * size of the union sparsity pattern of C and the A_i, and ||C||_F.  Any
+ * output pointer may be NULL.  Returns PROXSDP_ERR_INVALID_ARG on malformed
+ * input (same checks as set_problem). */
+int proxsdp_gpu_analyze_problem(const proxsdp_gpu_settings* settings, int64_t n, const double* C_dense,
+                                int64_t c_nnz, const int64_t* c_idx, const double* c_val,
+                                int64_t m_total, int64_t m_eq, const int64_t* A_rowptr,
+                                const int64_t* A_col, const double* A_val, const double* rhs,
+                                double* norm_M, double* alpha, int64_t* n_union, double* norm_C);
+
 /* Run Alg. 2 (or Alg. 1 with full_eig) from X = 0, y = 0 until convergence or a
  * cap.  `info` may be NULL. */
 int proxsdp_gpu_solve(proxsdp_gpu_t h, proxsdp_gpu_info* info);

@@ -15,6 +15,7 @@ from ._binding import (  # noqa: F401
     ProxSDPError,
     Settings,
     Solver,
+    analyze_problem,
     aproj,
     block_matvec,
     default_settings,

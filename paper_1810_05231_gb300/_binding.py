@@ -42,6 +42,7 @@ EXPORTED = [
     "proxsdp_gpu_aproj",
     "proxsdp_gpu_block_matvec",
     "proxsdp_gpu_sym_eig",
+    "proxsdp_gpu_analyze_problem",
 ]
 
 
@@ -125,6 +126,9 @@ def lib():
                                     ctypes.POINTER(Info)]
     L.proxsdp_gpu_block_matvec.argtypes = [vp, i64, i64, vp, i64, i32, vp, i64, vp]
     L.proxsdp_gpu_sym_eig.argtypes = [vp, i32, vp, vp, vp]
+    L.proxsdp_gpu_analyze_problem.argtypes = [ctypes.POINTER(Settings), i64, dp, i64, dp, dp, i64, i64, dp, dp, dp,
+                                              dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     for name in EXPORTED:
         if name not in ("proxsdp_gpu_destroy", "proxsdp_gpu_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -236,6 +240,22 @@ class Solver:
                self.h)
         rr = int(r.value)
         return dict(X=X, y=y[:m], V=V[: n * rr].reshape(rr, n).T.copy(), lam=lam[:rr].copy(), r=rr)
+
+
+def analyze_problem(n, m_eq, A_rowptr, A_col, A_val, rhs, C_dense=None, C_idx=None, C_val=None,
+                    settings: Settings | None = None):
+    """Host-only validation and preprocessing (no GPU): returns
+    dict(norm_M, alpha, n_union, norm_C); raises ProxSDPError on bad input."""
+    rowptr, col, val, b = _i64(A_rowptr), _i64(A_col), _f64(A_val), _f64(rhs)
+    Cd, ci, cv = _f64(C_dense), _i64(C_idx), _f64(C_val)
+    c_nnz = 0 if ci is None else int(ci.shape[0])
+    nm, al, nc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    nu = ctypes.c_int64()
+    _check(lib().proxsdp_gpu_analyze_problem(ctypes.byref(settings) if settings is not None else None, int(n),
+                                             _ptr(Cd), c_nnz, _ptr(ci), _ptr(cv), int(b.shape[0]), int(m_eq),
+                                             _ptr(rowptr), _ptr(col), _ptr(val), _ptr(b), ctypes.byref(nm),
+                                             ctypes.byref(al), ctypes.byref(nu), ctypes.byref(nc)))
+    return dict(norm_M=nm.value, alpha=al.value, n_union=nu.value, norm_C=nc.value)
 
 
 def _torch_stream(stream):

@@ -187,7 +187,7 @@ int preprocess(const proxsdp_gpu_settings& set, int64_t n64, const double* C_den
   for (size_t d = 0; d < h.dense_row.size(); ++d) h.dense_a[d] *= h.scale[h.dense_row[d]];
   // extended rows (constraints, then the objective) and their chunks
   h.row_chunk.assign(m + 2, 0);
-  auto push_row = [&](const std::vector<Entry>& v, double s) {
+  auto push_row = [&](const std::vector<Entry>& v, double s, int row) {
     int64_t b = (int64_t)h.ent_p.size();
     for (const Entry& x : v) {
       int p, q;
@@ -197,17 +197,21 @@ int preprocess(const proxsdp_gpu_settings& set, int64_t n64, const double* C_den
       h.ent_a.push_back(x.a * s * (p == q ? 1.0 : 2.0));
     }
     int64_t e = (int64_t)h.ent_p.size();
-    for (int64_t c = b; c < e; c += psdp::kChunk) {
+    int64_t c = b;
+    do {  // every row owns at least one (possibly empty) chunk
       h.chunk_beg.push_back((int)c);
       h.chunk_end.push_back((int)std::min<int64_t>(e, c + psdp::kChunk));
-    }
+      h.chunk_row.push_back(row);
+      c += psdp::kChunk;
+    } while (c < e);
   };
   for (int i = 0; i < m; ++i) {
     h.row_chunk[i] = (int)h.chunk_beg.size();
-    push_row(rows[i], h.scale[i]);
+    push_row(rows[i], h.scale[i], i);
+    if ((int)h.chunk_beg.size() - h.row_chunk[i] > 1) h.multi_rows.push_back(i);
   }
   h.row_chunk[m] = (int)h.chunk_beg.size();
-  push_row(centries, 1.0);
+  push_row(centries, 1.0, m);
   h.row_chunk[m + 1] = (int)h.chunk_beg.size();
   // union pattern of C and the constraint entries
   struct Contrib {
@@ -449,6 +453,33 @@ int proxsdp_gpu_set_problem(proxsdp_gpu_t h, int64_t n, const double* C_dense, i
   if (S.set.full_eig && n > psdp::kFullEigMax)
     return S.fail(PROXSDP_ERR_UNSUPPORTED, "full_eig (Alg. 1) is limited to n <= 128");
   return S.upload(hp);
+}
+
+int proxsdp_gpu_analyze_problem(const proxsdp_gpu_settings* settings, int64_t n, const double* C_dense,
+                                int64_t c_nnz, const int64_t* c_idx, const double* c_val, int64_t m_total,
+                                int64_t m_eq, const int64_t* A_rowptr, const int64_t* A_col,
+                                const double* A_val, const double* rhs, double* norm_M, double* alpha,
+                                int64_t* n_union, double* norm_C) {
+  proxsdp_gpu_settings s;
+  if (settings) s = *settings;
+  else proxsdp_gpu_settings_default(&s);
+  std::string err;
+  int rc = check_settings(s, err);
+  if (rc) {
+    g_last_create_error = err;
+    return rc;
+  }
+  HostProblem hp;
+  rc = preprocess(s, n, C_dense, c_nnz, c_idx, c_val, m_total, m_eq, A_rowptr, A_col, A_val, rhs, hp, err);
+  if (rc) {
+    g_last_create_error = err;
+    return rc;
+  }
+  if (norm_M) *norm_M = hp.normM;
+  if (alpha) *alpha = hp.alpha;
+  if (n_union) *n_union = (int64_t)hp.u_p.size();
+  if (norm_C) *norm_C = hp.normC;
+  return PROXSDP_OK;
 }
 
 int proxsdp_gpu_solve(proxsdp_gpu_t h, proxsdp_gpu_info* info) {

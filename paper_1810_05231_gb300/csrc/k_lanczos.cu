@@ -59,8 +59,10 @@ constexpr int MV_RB = 32, MV_CB = 16, MV_KC = 64;
 __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ S, int lds, int n,
                                                       const float* __restrict__ Q, int ldq,
                                                       float* __restrict__ W, int ldw, int k,
-                                                      const int* skip) {
+                                                      const int* skip, cudaGraphConditionalHandle cond,
+                                                      int set_cond) {
   if (skip && *(volatile const int*)skip) return;
+  if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 1u);
   __shared__ float Ss[MV_RB][MV_KC + 1];
   __shared__ float Qs[MV_KC][MV_CB + 1];
   const int tid = threadIdx.x;
@@ -96,9 +98,10 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
 }
 
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st) {
+                         int k, const int* skip, cudaStream_t st, cudaGraphConditionalHandle cond,
+                         int set_cond) {
   dim3 grid((n + MV_RB - 1) / MV_RB, (k + MV_CB - 1) / MV_CB);
-  k_block_matvec<<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, skip);
+  k_block_matvec<<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, skip, cond, set_cond);
 }
 
 // ---------------------------------------------------------------------------

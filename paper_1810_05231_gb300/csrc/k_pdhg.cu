@@ -114,6 +114,10 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     int i = o / w, t = o % w;
     if (i < rows) wk.Vrm[nw][(size_t)(r0 + i) * wk.ldv + t] = Vs[i * (w + 1) + t];
   }
+  for (int o = tid; o < RZ_RB * w; o += blockDim.x) {  // column-major slot of the new factors
+    int t = o / RZ_RB, i = o % RZ_RB;
+    if (i < rows) wk.Vcm[(size_t)(nw * kMaxR + t) * wk.ldq + r0 + i] = Vs[i * (w + 1) + t];
+  }
   // partial sums per Ritz column: ||wv - theta v||^2, v.wv, v.v, sum v
   double* part = wk.ritz_part + (size_t)blockIdx.x * 4 * kMaxW;
   for (int t = tid; t < w; t += blockDim.x) {
@@ -183,81 +187,88 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
 }
 
 // ---------------------------------------------------------------------------
-// M_ext(X) chunk partials: X = sum_{t<r} max(lambda_t,0) v_t v_t^T
+// M(X^{k+1}) from the factors, fused with the dual step (Alg. 2 dual step
+// parts 1 and 2) and its reductions
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_mx(DevProblem pb, DevWork wk, int r) {
+// X = sum_{t<r} max(lambda_t,0) v_t v_t^T; one warp per chunk of <= kChunk
+// entries of one extended row.  A row with one chunk is updated by that warp:
+//   y_half = y + alpha (2 M(X+) - M(X));  equality rows y+ = y_half - alpha b,
+//   inequality rows y+ = max(y_half - alpha h, 0)  (= y_half - alpha proj(y_half/alpha)).
+// Rows with several chunks and the objective row m are finished by the last block.
+__device__ __forceinline__ void dual_row(const DevProblem& pb, const DevWork& wk, int nw, int od, int row,
+                                         double mxn, int r, const float* lp, double (&v)[4]) {
+  const int d = pb.n_dense ? pb.dense_of_row[row] : -1;
+  if (d >= 0) {  // tr(a 11^T X) = a sum_t max(lambda_t,0) (1^T v_t)^2
+    double s = 0.0;
+    for (int t = 0; t < r; ++t) {
+      double cs = wk.colsum[nw][t];
+      s += (double)lp[t] * cs * cs;
+    }
+    mxn += pb.dense_a[d] * s;
+  }
+  const double alpha = pb.alpha;
+  const double mxo = wk.mx[od][row];
+  const double yo = wk.y[row];
+  const double yh = yo + alpha * (2.0 * mxn - mxo);
+  const double yn = (row < pb.m_eq) ? yh - alpha * pb.rhs[row] : fmax(yh - alpha * pb.rhs[row], 0.0);
+  const double dyv = yn - yo;
+  wk.y[row] = yn;
+  wk.dy[row] = dyv;
+  wk.mx[nw][row] = mxn;
+  const double dmx = mxn - mxo;
+  const double ed = dyv / alpha - dmx;
+  v[0] += ed * ed;          // eps_dual^2
+  v[1] += dyv * dmx;        // <dy, M(dX)> = <M*(dy), dX>
+  v[2] += pb.rhs[row] * yn; // rhs^T y
+}
+
+__global__ void __launch_bounds__(256) k_mxdual(DevProblem pb, DevWork wk, int r) {
   __shared__ float lp[kMaxR];
-  const int nw = 1 - wk.ctl->par;
+  __shared__ double sh[32 * 4];
+  Ctl* ctl = wk.ctl;
+  const int nw = 1 - ctl->par, od = ctl->par;
   for (int t = threadIdx.x; t < kMaxR; t += blockDim.x) lp[t] = (t < r) ? (float)fmax(wk.lam[nw][t], 0.0) : 0.f;
   __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= pb.n_chunks) return;
-  const float* V = wk.Vrm[nw];
-  double acc = 0.0;
-  for (int e = pb.chunk_beg[warp] + lane; e < pb.chunk_end[warp]; e += 32) {
-    const float* vp = V + (size_t)pb.ent_p[e] * wk.ldv;
-    const float* vq = V + (size_t)pb.ent_q[e] * wk.ldv;
-    float x = 0.f;
-#pragma unroll 8
-    for (int t = 0; t < r; ++t) x = fmaf(lp[t] * vp[t], vq[t], x);
-    acc += pb.ent_a[e] * (double)x;
-  }
-  acc = warp_sum(acc);
-  if (lane == 0) wk.chunk_part[warp] = acc;
-}
-
-// ---------------------------------------------------------------------------
-// dual step (Alg. 2 dual parts 1 and 2) and its reductions
-// ---------------------------------------------------------------------------
-// y_half = y + alpha (2 M(X+) - M(X)); equality rows y+ = y_half - alpha b,
-// inequality rows y+ = max(y_half - alpha h, 0)  (= y_half - alpha proj(y_half/alpha)).
-__global__ void __launch_bounds__(256) k_dual(DevProblem pb, DevWork wk, int r) {
-  __shared__ double sh[32 * 4];
-  Ctl* ctl = wk.ctl;
-  const int nw = 1 - ctl->par, od = ctl->par;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double alpha = pb.alpha;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (i < pb.m) {
-    double mxn = 0.0;
-    for (int c = pb.row_chunk[i]; c < pb.row_chunk[i + 1]; ++c) mxn += wk.chunk_part[c];
-    if (pb.n_dense) {
-      const int d = pb.dense_of_row[i];
-      if (d >= 0) {  // tr(a 11^T X) = a sum_t max(lambda_t,0) (1^T v_t)^2
-        double s = 0.0;
-        for (int t = 0; t < r; ++t) {
-          double cs = wk.colsum[nw][t];
-          s += fmax(wk.lam[nw][t], 0.0) * cs * cs;
-        }
-        mxn += pb.dense_a[d] * s;
-      }
+  if (warp < pb.n_chunks) {
+    const float* V = wk.Vrm[nw];
+    double acc = 0.0;
+    for (int e = pb.chunk_beg[warp] + lane; e < pb.chunk_end[warp]; e += 32) {
+      const float* vp = V + (size_t)pb.ent_p[e] * wk.ldv;
+      const float* vq = V + (size_t)pb.ent_q[e] * wk.ldv;
+      float x = 0.f;
+#pragma unroll 8
+      for (int t = 0; t < r; ++t) x = fmaf(lp[t] * vp[t], vq[t], x);
+      acc += pb.ent_a[e] * (double)x;
     }
-    const double mxo = wk.mx[od][i];
-    const double yo = wk.y[i];
-    const double yh = yo + alpha * (2.0 * mxn - mxo);
-    const double yn = (i < pb.m_eq) ? yh - alpha * pb.rhs[i] : fmax(yh - alpha * pb.rhs[i], 0.0);
-    const double dyv = yn - yo;
-    wk.y[i] = yn;
-    wk.dy[i] = dyv;
-    wk.mx[nw][i] = mxn;
-    const double dmx = mxn - mxo;
-    const double ed = dyv / alpha - dmx;
-    v[0] = ed * ed;           // eps_dual^2
-    v[1] = dyv * dmx;         // <dy, M(dX)> = <M*(dy), dX>
-    v[2] = pb.rhs[i] * yn;    // rhs^T y
+    acc = warp_sum(acc);
+    const int row = pb.chunk_row[warp];
+    const bool single = row < pb.m && (pb.row_chunk[row + 1] - pb.row_chunk[row] == 1);
+    if (lane == 0) {
+      if (single) dual_row(pb, wk, nw, od, row, acc, r, lp, v);
+      else wk.chunk_part[warp] = acc;
+    }
   }
   block_sum<4>(v, sh);
-  double* part = wk.part + (size_t)blockIdx.x * 4;
   if (threadIdx.x == 0)
-    for (int k = 0; k < 4; ++k) part[k] = v[k];
+    for (int k = 0; k < 4; ++k) wk.part[(size_t)blockIdx.x * 4 + k] = v[k];
   if (!last_block(&wk.counters[CNT_DUAL * 512])) return;
+  // rows spread over several chunks
+  double u[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int k = threadIdx.x; k < pb.n_multi; k += blockDim.x) {
+    const int row = pb.multi_rows[k];
+    double mxn = 0.0;
+    for (int c = pb.row_chunk[row]; c < pb.row_chunk[row + 1]; ++c) mxn += __ldcg(&wk.chunk_part[c]);
+    dual_row(pb, wk, nw, od, row, mxn, r, lp, u);
+  }
+  block_sum<4>(u, sh);
   if (threadIdx.x == 0) {
-    double s[4] = {0, 0, 0, 0};
+    double s[3] = {u[0], u[1], u[2]};
     for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int k = 0; k < 4; ++k) s[k] += __ldcg(&wk.part[(size_t)b * 4 + k]);
-    // objective row m: tr(C X+)
-    double pobj = 0.0;
+      for (int k = 0; k < 3; ++k) s[k] += __ldcg(&wk.part[(size_t)b * 4 + k]);
+    double pobj = 0.0;  // objective row m: tr(C X+)
     for (int c = pb.row_chunk[pb.m]; c < pb.row_chunk[pb.m + 1]; ++c) pobj += __ldcg(&wk.chunk_part[c]);
     wk.mx[nw][pb.m] = pobj;
     ctl->red_dual[0] = s[0];
@@ -318,8 +329,8 @@ __global__ void __launch_bounds__(256) k_dvals(DevProblem pb, DevWork wk) {
 // G is the Gram of the column-major factor slots [slot0 | slot1] (2*kMaxR
 // columns); X = V_s Lambda_+ V_s^T for slot s, so
 // ||X1 - X0||_F^2 = sum lam1 lam1 G11^2 + sum lam0 lam0 G00^2 - 2 sum lam1 lam0 G10^2.
-__global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, const double* G,
-                                                 cudaGraphConditionalHandle cond, int use_cond) {
+__device__ void control_tail(const DevProblem& pb, const DevWork& wk, const double* G,
+                             cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sh[32 * 3];
   Ctl* ctl = wk.ctl;
   const int nw = 1 - ctl->par, od = ctl->par;
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, cons
   ctl->lam_r = lam_r;
   ctl->normX = normX;
   ctl->matvecs += 1;  // warm-start product of the next iteration
-  ctl->launches += ctl->full_eig_path ? 10 : 12;  // per-iteration kernels outside the restart cycles
+  ctl->launches += ctl->full_eig_path ? 7 : 8;  // per-iteration kernels outside the restart cycles
   const double comb = eps_p + eps_d;
   const int win = ctl->window;
   const double old = ctl->hist[it % win];
@@ -411,6 +422,86 @@ __global__ void __launch_bounds__(256) k_control(DevProblem pb, DevWork wk, cons
   ctl->lz_done = 0;    // next projection starts
   ctl->lz_cycle = 0;
   if (use_cond) cudaGraphSetConditional(cond, status == ST_RUNNING ? 1u : 0u);
+}
+
+
+// Gram of the factor slots (only the first `act` columns of each slot; the
+// deterministic split-row reduction of the Lanczos Gram kernel) followed, in
+// the last block to finish, by the controller.
+constexpr int GC_T = 16, GC_RC = 64;
+
+struct DFc {
+  float hi, lo;
+  __device__ __forceinline__ DFc() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void fma_acc(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = fmaf(a, b, -p);
+    float s = __fadd_rn(hi, p);
+    float bb = __fsub_rn(s, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk, int act, int rows_per_split,
+                                                      cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ float As[GC_RC][GC_T + 1];
+  __shared__ float Bs[GC_RC][GC_T + 1];
+  __shared__ unsigned s_last;
+  const int tid = threadIdx.x;
+  const int n = pb.n;
+  const int slot = kMaxR, ka = 2 * kMaxR;
+  const int per = (act + GC_T - 1) / GC_T;
+  const int tiles_b = per * 2;
+  const int ta = blockIdx.x / tiles_b, tb = blockIdx.x % tiles_b;
+  const int a0 = (ta / per) * slot + (ta % per) * GC_T;
+  const int b0 = (tb / per) * slot + (tb % per) * GC_T;
+  const int ty = tid / GC_T, tx = tid % GC_T;
+  const int rbeg = blockIdx.y * rows_per_split;
+  const int rend = min(n, rbeg + rows_per_split);
+  const float* A = wk.Vcm;
+  const int lda = wk.ldq;
+  DFc acc;
+  for (int i0 = rbeg; i0 < rend; i0 += GC_RC) {
+    for (int idx = tid; idx < GC_RC * GC_T; idx += 256) {
+      int c = idx / GC_RC, i = idx % GC_RC;
+      int gi = i0 + i;
+      As[i][c] = (gi < rend) ? A[(size_t)(a0 + c) * lda + gi] : 0.f;
+      Bs[i][c] = (gi < rend) ? A[(size_t)(b0 + c) * lda + gi] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int i = 0; i < GC_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
+    __syncthreads();
+  }
+  double* part = wk.part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (GC_T * GC_T);
+  part[tid] = acc.value();
+  unsigned* cnt = wk.counters + CNT_CTL * 512;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&cnt[blockIdx.x], 1u) == gridDim.y - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  {
+    double s = 0.0;
+    const double* base = wk.part + (size_t)blockIdx.x * gridDim.y * (GC_T * GC_T);
+    for (int sp = 0; sp < (int)gridDim.y; ++sp) s += __ldcg(&base[(size_t)sp * (GC_T * GC_T) + tid]);
+    wk.Hx[(size_t)(a0 + ty) * ka + b0 + tx] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    cnt[blockIdx.x] = 0u;
+    s_last = (atomicAdd(&cnt[511], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (tid == 0) cnt[511] = 0u;
+  control_tail(pb, wk, wk.Hx, cond, use_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -483,15 +574,6 @@ __global__ void k_copy_cols(const float* src, int lds_, float* dst, int ldd, int
   dst[(size_t)c * ldd + i] = src[(size_t)c * lds_ + i];
 }
 
-// column-major factor slot of the new iterate <- first w columns of Q
-__global__ void k_save_factor_cm(DevWork wk, float* Vcm, int n, int w) {
-  const int nw = 1 - wk.ctl->par;
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)n * kMaxR) return;
-  int c = (int)(idx / n), i = (int)(idx % n);
-  Vcm[(size_t)(nw * kMaxR + c) * wk.ldq + i] = (c < w) ? wk.Q[(size_t)c * wk.ldq + i] : 0.f;
-}
-
 // Full projection (n <= 128): eigenvectors of S from the dense Jacobi solve
 // become the factors of the new iterate (all n of them).
 __global__ void k_full_eig_factors(DevWork wk, int n) {
@@ -501,7 +583,10 @@ __global__ void k_full_eig_factors(DevWork wk, int n) {
     int i = idx / kMaxR, t = idx % kMaxR;
     float v = (t < n) ? wk.Y[(size_t)t * kMaxK + i] : 0.f;
     wk.Vrm[nw][(size_t)i * wk.ldv + t] = v;
-    if (t < n) wk.Q[(size_t)t * wk.ldq + i] = v;
+    if (t < n) {
+      wk.Q[(size_t)t * wk.ldq + i] = v;
+      wk.Vcm[(size_t)(nw * kMaxR + t) * wk.ldq + i] = v;
+    }
   }
   if (blockIdx.x == 0) {
     for (int t = threadIdx.x; t < kMaxR; t += blockDim.x) {
@@ -523,10 +608,6 @@ __global__ void k_s_to_t(const float* S, int lds, int n, double* T) {
   if (idx >= n * n) return;
   int i = idx / n, j = idx % n;
   T[idx] = (double)S[(size_t)i * lds + j];
-}
-
-__global__ void k_iter_begin(cudaGraphConditionalHandle inner, int use_cond) {
-  if (use_cond) cudaGraphSetConditional(inner, 1u);
 }
 
 __global__ void k_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change) {
@@ -575,16 +656,10 @@ void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
   k_ritz<<<blocks, 256, ritz_smem(K, w), st>>>(wk, n, K, w, r, s_steps, cond, use_cond);
 }
 
-void launch_mx(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
-  if (pb.n_chunks == 0) return;
+void launch_mxdual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
   int blocks = (pb.n_chunks * 32 + 255) / 256;
-  k_mx<<<blocks, 256, 0, st>>>(pb, wk, r);
-}
-
-void launch_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
-  int blocks = (pb.m + 255) / 256;
   if (blocks < 1) blocks = 1;
-  k_dual<<<blocks, 256, 0, st>>>(pb, wk, r);
+  k_mxdual<<<blocks, 256, 0, st>>>(pb, wk, r);
 }
 
 void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st) {
@@ -593,9 +668,17 @@ void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st) {
   k_dvals<<<blocks, 256, 0, st>>>(pb, wk);
 }
 
-void launch_control(const DevProblem& pb, const DevWork& wk, const double* G,
-                    cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
-  k_control<<<1, 256, 0, st>>>(pb, wk, G, cond, use_cond);
+void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
+                         cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
+  const int per = (act + GC_T - 1) / GC_T;
+  const int tiles = per * 2 * per * 2;
+  int nsplit = 148 / tiles;
+  if (nsplit < 1) nsplit = 1;
+  int rows = (pb.n + nsplit - 1) / nsplit;
+  if (rows < 128) rows = 128;
+  nsplit = (pb.n + rows - 1) / rows;
+  if (nsplit < 1) nsplit = 1;
+  k_gram_control<<<dim3(tiles, nsplit), 256, 0, st>>>(pb, wk, act, rows, cond, use_cond);
 }
 
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st) {
@@ -610,23 +693,12 @@ void launch_copy_cols(const float* src, int lds, float* dst, int ldd, int n, int
   k_copy_cols<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(src, lds, dst, ldd, n, k, skip);
 }
 
-void launch_save_factor(const DevWork& wk, float* Vcm, int n, int w, cudaStream_t st) {
-  size_t total = (size_t)n * kMaxR;
-  k_save_factor_cm<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(wk, Vcm, n, w);
-}
-
 void launch_full_eig_factors(const DevWork& wk, int n, cudaStream_t st) {
   k_full_eig_factors<<<32, 256, 0, st>>>(wk, n);
 }
 
 void launch_s_to_t(const float* S, int lds, int n, double* T, cudaStream_t st) {
   k_s_to_t<<<(n * n + 255) / 256, 256, 0, st>>>(S, lds, n, T);
-}
-
-void launch_iter_begin(const DevWork& wk, cudaGraphConditionalHandle inner, int use_cond,
-                       cudaStream_t st) {
-  (void)wk;
-  k_iter_begin<<<1, 1, 0, st>>>(inner, use_cond);
 }
 
 void launch_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change,

@@ -76,7 +76,10 @@ struct DevProblem {
   int n_chunks;                // work chunks of <= kChunk entries of one row
   const int* chunk_beg;
   const int* chunk_end;
-  const int* row_chunk;        // m + 2: chunks of row i are [row_chunk[i], row_chunk[i+1])
+  const int* row_chunk;        // m + 2: chunks of row i are [row_chunk[i], row_chunk[i+1]) (>= 1 each)
+  const int* chunk_row;        // row of each chunk
+  int n_multi;                 // constraint rows with more than one chunk
+  const int* multi_rows;
   const double* rhs;           // m (scaled)
   int n_dense;                 // structured rows a * 11^T
   const int* dense_row;
@@ -119,6 +122,8 @@ struct DevWork {
   float* Y;  double* theta;    // Ritz solve output (kMaxK x kMaxK), values
   double* ritz_part;           // partials of the Ritz kernel
   unsigned* counters;          // last-block counters (512 per kernel kind)
+  float* Vcm;                  // column-major factor slots [slot 0 | slot 1], kMaxR columns each
+  double* Hx;                  // Gram of the factor slots (2 kMaxR)^2
   Ctl* ctl;
 };
 
@@ -128,7 +133,8 @@ enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_NUM }
 // launchers (k_lanczos.cu)
 // ---------------------------------------------------------------------------
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st);
+                         int k, const int* skip, cudaStream_t st,
+                         cudaGraphConditionalHandle cond = 0, int set_cond = 0);
 void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
                          cudaStream_t st);
 // H = A^T B (ka x kb, FP64 row-major) with deterministic block reduction.
@@ -154,20 +160,18 @@ void init_lanczos_attributes();
 // ---------------------------------------------------------------------------
 void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
-void launch_mx(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
-void launch_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
+// M(X^{k+1}) from the factors fused with the dual step and its reductions.
+void launch_mxdual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
 void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st);
-void launch_control(const DevProblem& pb, const DevWork& wk, const double* G,
-                    cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+// Gram of the factor slots (columns < act of each slot) fused with the controller.
+void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
+                         cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 // sel = 0: factors of the current iterate (Ctl::par); sel = 1: the other buffer.
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st);
 void launch_copy_cols(const float* src, int lds, float* dst, int ldd, int n, int k, const int* skip,
                       cudaStream_t st);
-void launch_save_factor(const DevWork& wk, float* Vcm, int n, int w, cudaStream_t st);
 void launch_full_eig_factors(const DevWork& wk, int n, cudaStream_t st);
 void launch_s_to_t(const float* S, int lds, int n, double* T, cudaStream_t st);
-void launch_iter_begin(const DevWork& wk, cudaGraphConditionalHandle inner, int use_cond,
-                       cudaStream_t st);
 void launch_ctl_set(Ctl* ctl, int status, int it_stop, int r, int w, int K, int k_change,
                     cudaStream_t st);
 void init_pdhg_attributes();

@@ -147,6 +147,9 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   CKA(dupload(allocs, &P.chunk_beg, h.chunk_beg, st));
   CKA(dupload(allocs, &P.chunk_end, h.chunk_end, st));
   CKA(dupload(allocs, &P.row_chunk, h.row_chunk, st));
+  CKA(dupload(allocs, &P.chunk_row, h.chunk_row, st));
+  P.n_multi = (int)h.multi_rows.size();
+  CKA(dupload(allocs, &P.multi_rows, h.multi_rows, st));
   CKA(dupload(allocs, &P.rhs, h.rhs, st));
   P.n_dense = (int)h.dense_row.size();
   CKA(dupload(allocs, &P.dense_row, h.dense_row, st));
@@ -199,6 +202,8 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   CKA(dalloc(allocs, &Wk.ctl, 1));
   CKA(dalloc(allocs, &Vcm, (size_t)ld * 2 * kMaxR));
   CKA(dalloc(allocs, &Hx, (size_t)4 * kMaxR * kMaxR));
+  Wk.Vcm = Vcm;
+  Wk.Hx = Hx;
   CK(cudaMemsetAsync(Wk.counters, 0, sizeof(unsigned) * CNT_NUM * 512, st));
   CK(cudaMemsetAsync(Wk.Q, 0, sizeof(float) * (size_t)ld * kMaxK, st));
   CK(cudaMemsetAsync(Wk.W, 0, sizeof(float) * (size_t)ld * kMaxK, st));
@@ -299,10 +304,9 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   } else {
     g_debug_n = n;
     enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
-    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st);
+    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, inner, use);
     dbg(wk, "warm matvec", st);
     if (in_graph) {
-      launch_iter_begin(wk, inner, 1, st);
       cudaStreamCaptureStatus cs;
       cudaGraph_t g;
       const cudaGraphNode_t* deps = nullptr;
@@ -327,16 +331,12 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
     }
   }
   dbg(wk, "projection", st);
-  launch_save_factor(wk, Vcm, n, k.full ? n : k.w, st);
-  launch_mx(pb, wk, k.r, st);
-  launch_dual(pb, wk, k.r, st);
+  launch_mxdual(pb, wk, k.r, st);
   launch_dvals(pb, wk, st);
-  dbg(wk, "mx/dual/dvals", st);
+  dbg(wk, "mxdual/dvals", st);
   const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
-  launch_gram(Vcm, wk.ldq, 2 * kMaxR, Vcm, wk.ldq, 2 * kMaxR, n, Hx, wk.part,
-              wk.counters + CNT_CTL * 512, nullptr, st, act, kMaxR);
-  launch_control(pb, wk, Hx, outer, use, st);
-  dbg(wk, "control", st);
+  launch_gram_control(pb, wk, act, outer, use, st);
+  dbg(wk, "gram+control", st);
   launch_rebuild(pb, wk, k.r, 0, st);
   dbg(wk, "rebuild", st);
   CK(cudaGetLastError());

@@ -20,7 +20,7 @@ struct HostProblem {
   int n = 0, m = 0, m_eq = 0;
   std::vector<int> ent_p, ent_q;
   std::vector<double> ent_a;  // extended rows: constraints then the objective row
-  std::vector<int> chunk_beg, chunk_end, row_chunk;
+  std::vector<int> chunk_beg, chunk_end, row_chunk, chunk_row, multi_rows;
   std::vector<double> rhs, scale;
   std::vector<int> dense_row, dense_of_row;
   std::vector<double> dense_a;
