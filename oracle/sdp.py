@@ -307,7 +307,9 @@ def solve(prob_in: Problem, mode="lr", tol=1e-4, max_iter=100000, rank_init=8,
     * start ``X = 0``, ``y = 0``;
     * rows scaled to unit Frobenius norm, ``alpha = alpha_frac / ||M||_2``
       (the step condition ``0 < alpha < 1/||M||_2`` of Sec. 2.2);
-    * stop when ``max(rel_primal, rel_dual, rel_gap) <= tol`` with
+    * the inner loop of Alg. 2 ends when ``max(rel_primal, rel_dual) <= tol``; the
+      solve stops there when, in addition, the rank is sufficient and
+      ``rel_gap <= tol`` (otherwise it keeps iterating at the same rank), with
       ``rel_primal = eps_primal / (1 + ||C||_F)``,
       ``rel_dual = eps_dual / (1 + ||rhs||_2)`` and
       ``rel_gap = |pobj - dobj| / (1 + |pobj| + |dobj|)``,
@@ -360,11 +362,12 @@ def solve(prob_in: Problem, mode="lr", tol=1e-4, max_iter=100000, rank_init=8,
         if record_history:
             history.append(dict(it=it, r=r, rel_p=rel_p, rel_d=rel_d, rel_gap=rel_gap,
                                 pobj=pobj, lam_r=float(lam_r)))
-        converged = max(rel_p, rel_d, rel_gap) <= tol
+        converged = max(rel_p, rel_d) <= tol  # the inner-loop test of Alg. 2 (relative residuals)
         if converged and rank_ok:
-            status = CONVERGED
-            break
-        if converged:  # Alg. 2: save the feasible pair, then double the target rank
+            if rel_gap <= tol:
+                status = CONVERGED
+                break
+        elif converged:  # Alg. 2: save the feasible pair, then double the target rank
             saved.append((it, r))
             if r >= max_rank:
                 status = STALLED_AT_MAX_RANK

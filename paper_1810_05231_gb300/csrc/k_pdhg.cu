@@ -398,12 +398,14 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
       !(lam_r == lam_r) || fabs(pobj) > 1e300) {
     status = ST_NUMERIC;
   } else {
-    const bool conv = fmax(rel_p, fmax(rel_d, rel_gap)) <= ctl->tol;
+    // inner-loop test of Alg. 2 on the relative residuals; the final stop also
+    // needs a sufficient rank and a small relative gap
+    const bool conv = fmax(rel_p, rel_d) <= ctl->tol;
     const bool rank_ok = (r >= n) || ctl->full_eig ||
                          (sqrt((double)(n - r)) * fmax(lam_r, 0.0) <= ctl->eps_lambda * fmax(1.0, normX));
     bool grow = false;
     if (conv && rank_ok) {
-      status = ST_CONVERGED;
+      if (rel_gap <= ctl->tol) status = ST_CONVERGED;
     } else if (conv) {
       ctl->saved += 1;  // feasible (X_[r], y_[r]) of Alg. 2
       grow = true;
