@@ -445,32 +445,45 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
         qq[tid] = q;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * Kp; idx += nth) {  // rows: A <- J^T A
-        int t = idx / Kp, j = idx % Kp;
-        float c = cs[t], s = sn[t];
-        if (s == 0.f) continue;
-        int p = pp[t], q = qq[t];
-        float ap = A[p * ld + j], aq = A[q * ld + j];
-        A[p * ld + j] = c * ap - s * aq;
-        A[q * ld + j] = s * ap + c * aq;
+      // A <- J^T A J: every 2x2 block (pair t rows, pair u columns) transforms
+      // independently, B <- J_t^T B J_u; blocks t <= u, mirrored.
+      const int nblk = half * (half + 1) / 2;
+      for (int idx = tid; idx < nblk; idx += nth) {
+        int t = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
+        while (t * (t + 1) / 2 > idx) --t;
+        while ((t + 1) * (t + 2) / 2 <= idx) ++t;
+        const int u = idx - t * (t + 1) / 2;  // u <= t
+        const float ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
+        if (st == 0.f && su == 0.f) continue;
+        const int pt = pp[t], qt = qq[t], pu = pp[u], qu = qq[u];
+        float b00 = A[pt * ld + pu], b01 = A[pt * ld + qu], b10 = A[qt * ld + pu], b11 = A[qt * ld + qu];
+        float m00 = ct * b00 - st * b10, m01 = ct * b01 - st * b11;
+        float m10 = st * b00 + ct * b10, m11 = st * b01 + ct * b11;
+        float n00 = cu * m00 - su * m01, n01 = su * m00 + cu * m01;
+        float n10 = cu * m10 - su * m11, n11 = su * m10 + cu * m11;
+        if (t == u) {  // the rotation annihilates the pair's off-diagonal entry
+          n01 = 0.f;
+          n10 = 0.f;
+        }
+        A[pt * ld + pu] = n00;
+        A[pt * ld + qu] = n01;
+        A[qt * ld + pu] = n10;
+        A[qt * ld + qu] = n11;
+        if (t != u) {
+          A[pu * ld + pt] = n00;
+          A[qu * ld + pt] = n01;
+          A[pu * ld + qt] = n10;
+          A[qu * ld + qt] = n11;
+        }
       }
-      __syncthreads();
-      for (int idx = tid; idx < half * Kp; idx += nth) {  // columns: A <- A J, V <- V J
-        int t = idx / Kp, i = idx % Kp;
-        float c = cs[t], s = sn[t];
+      for (int idx = tid; idx < half * Kp; idx += nth) {  // V <- V J
+        int u = idx / Kp, i = idx % Kp;
+        float c = cs[u], s = sn[u];
         if (s == 0.f) continue;
-        int p = pp[t], q = qq[t];
-        float ap = A[i * ld + p], aq = A[i * ld + q];
-        A[i * ld + p] = c * ap - s * aq;
-        A[i * ld + q] = s * ap + c * aq;
+        int p = pp[u], q = qq[u];
         float vp = V[i * ld + p], vq = V[i * ld + q];
         V[i * ld + p] = c * vp - s * vq;
         V[i * ld + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      if (tid < half) {
-        A[pp[tid] * ld + qq[tid]] = 0.f;
-        A[qq[tid] * ld + pp[tid]] = 0.f;
       }
       __syncthreads();
     }
@@ -489,6 +502,14 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
       rk += (dj > di) || (dj == di && j < i);
     }
     rank[i] = rk;
+  }
+  __syncthreads();
+  // T (symmetrised, FP64) as a packed upper triangle in the freed A region
+  // (Kp (Kp+1)/2 doubles = Kp (Kp+1) floats)
+  double* Tp = reinterpret_cast<double*>(A);
+  for (int idx = tid; idx < K * K; idx += nth) {
+    int i = idx / K, j = idx % K;
+    if (i <= j) Tp[j * (j + 1) / 2 + i] = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
   }
   __syncthreads();
   // refinement scratch, per pass: Ph | Pl | Sm | Rm  (each Kp x jb floats)
@@ -510,7 +531,7 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
       const int j = wanted[jj];
       DF acc;
       for (int l = 0; l < K; ++l) {
-        double t = 0.5 * (Tin[k * K + l] + Tin[l * K + k]);
+        double t = (k <= l) ? Tp[l * (l + 1) / 2 + k] : Tp[k * (k + 1) / 2 + l];
         float hi = (float)t;
         float lo = (float)(t - (double)hi);
         float y = V[l * ld + j];

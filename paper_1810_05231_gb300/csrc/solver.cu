@@ -326,8 +326,16 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
       enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 1, st_aux);
       CK(cudaStreamEndCapture(st_aux, &body));
     } else {
-      for (int c = 0; c < std::max(1, set.lanczos_max_cycles); ++c)
-        enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed + 977ULL * (unsigned long long)c, inner, 0, st);
+      // direct launches: the same kernels as the graph body, with the host
+      // reading the projection's convergence flag after every restart cycle
+      for (int c = 0; c < std::max(1, set.lanczos_max_cycles); ++c) {
+        enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 0, st);
+        int done = 0;
+        CK(cudaMemcpyAsync(&ctl_host->lz_done, &wk.ctl->lz_done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        done = ctl_host->lz_done;
+        if (done) break;
+      }
     }
   }
   dbg(wk, "projection", st);
