@@ -602,8 +602,21 @@ int proxsdp_gpu_block_matvec(const float* S, int64_t n, int64_t lds, const float
   if (cudaGetDevice(&dev) != cudaSuccess) return PROXSDP_ERR_CUDA;
   int rc = check_device(dev, err);
   if (rc) return rc;
-  psdp::launch_block_matvec(S, (int)lds, (int)n, Q, (int)ldq, W, (int)ldw, k, nullptr, (cudaStream_t)cuda_stream);
-  return cudaGetLastError() == cudaSuccess ? PROXSDP_OK : PROXSDP_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float* part = nullptr;
+  unsigned* cnt = nullptr;
+  const size_t np = psdp::block_matvec_scratch_floats((int)n, k), nc = psdp::block_matvec_counters((int)n, k);
+  if (cudaMallocAsync((void**)&part, np * sizeof(float), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&cnt, nc * sizeof(unsigned), st) != cudaSuccess) {
+    if (part) cudaFreeAsync(part, st);
+    return PROXSDP_ERR_OOM;
+  }
+  cudaMemsetAsync(cnt, 0, nc * sizeof(unsigned), st);
+  psdp::launch_block_matvec(S, (int)lds, (int)n, Q, (int)ldq, W, (int)ldw, k, nullptr, st, part, cnt);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(part, st);
+  cudaFreeAsync(cnt, st);
+  return e == cudaSuccess ? PROXSDP_OK : PROXSDP_ERR_CUDA;
 }
 
 int proxsdp_gpu_sym_eig(const double* T, int K, double* theta, float* Y, void* cuda_stream) {

@@ -12,6 +12,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace psdp {
 
 // ---------------------------------------------------------------------------
@@ -50,58 +52,137 @@ struct DF {
 };
 
 // ---------------------------------------------------------------------------
-// S * Q block product (SIMT version)
+// S * Q block product (SIMT, split over the inner dimension)
 // ---------------------------------------------------------------------------
-// CTA tile: 32 rows of S x 16 columns of Q, K-chunks of 64.  S symmetric, so
-// row blocks of S are also column blocks.
-constexpr int MV_RB = 32, MV_CB = 16, MV_KC = 64;
+// CTA tile: 128 rows of S x up to 64 columns of Q, over one slice [k0, k1) of
+// the inner dimension, in chunks of 32.  The S chunk is staged transposed
+// (Ss[k][row]) so a thread reads its 8 rows as two float4 broadcasts; each
+// thread accumulates 8 rows x G columns (G = column groups of 16).  Slices are
+// summed by the last CTA of each (row block, column block) in slice order
+// (deterministic).  S is symmetric, so its row blocks are also column blocks.
+constexpr int MV_RB = 128, MV_KC = 32, MV_LDS = 132;
 
+template <int G>
 __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ S, int lds, int n,
                                                       const float* __restrict__ Q, int ldq,
                                                       float* __restrict__ W, int ldw, int k,
-                                                      const int* skip, cudaGraphConditionalHandle cond,
-                                                      int set_cond) {
+                                                      int kslice, float* __restrict__ part,
+                                                      unsigned* counters, const int* skip,
+                                                      cudaGraphConditionalHandle cond, int set_cond) {
   if (skip && *(volatile const int*)skip) return;
-  if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 1u);
-  __shared__ float Ss[MV_RB][MV_KC + 1];
-  __shared__ float Qs[MV_KC][MV_CB + 1];
+  if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(cond, 1u);
+  __shared__ __align__(16) float Ss[MV_KC][MV_LDS];
+  __shared__ float Qs[MV_KC][16 * G + 1];
+  __shared__ unsigned s_last;
   const int tid = threadIdx.x;
+  const int tc = tid & 15, tr = tid >> 4;  // column within group, row group (8 rows)
   const int r0 = blockIdx.x * MV_RB;
-  const int c0 = blockIdx.y * MV_CB;
-  const int tx = tid % MV_CB, ty = tid / MV_CB;  // ty in [0,16)
-  float acc0 = 0.f, acc1 = 0.f;
-  for (int k0 = 0; k0 < n; k0 += MV_KC) {
+  const int c0 = blockIdx.z * 64;
+  const int kc = min(16 * G, k - c0);
+  const int kb = blockIdx.y * kslice, ke = min(n, kb + kslice);
+  float acc[8][G];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[a][g] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += MV_KC) {
+    // S chunk: 128 rows x 32 columns, coalesced along the row, stored transposed
     for (int idx = tid; idx < MV_RB * MV_KC; idx += 256) {
       int rr = idx / MV_KC, kk = idx % MV_KC;
       int gr = r0 + rr, gk = k0 + kk;
-      Ss[rr][kk] = (gr < n && gk < n) ? S[(size_t)gr * lds + gk] : 0.f;
+      Ss[kk][rr] = (gr < n && gk < ke) ? __ldg(&S[(size_t)gr * lds + gk]) : 0.f;
     }
-    for (int idx = tid; idx < MV_KC * MV_CB; idx += 256) {
+    for (int idx = tid; idx < MV_KC * 16 * G; idx += 256) {
       int cc = idx / MV_KC, kk = idx % MV_KC;
-      int gc = c0 + cc, gk = k0 + kk;
-      Qs[kk][cc] = (gc < k && gk < n) ? Q[(size_t)gc * ldq + gk] : 0.f;
+      int gk = k0 + kk;
+      Qs[kk][cc] = (cc < kc && gk < ke) ? __ldg(&Q[(size_t)(c0 + cc) * ldq + gk]) : 0.f;
     }
     __syncthreads();
-#pragma unroll 16
+#pragma unroll 4
     for (int kk = 0; kk < MV_KC; ++kk) {
-      float q = Qs[kk][tx];
-      acc0 = fmaf(Ss[ty][kk], q, acc0);
-      acc1 = fmaf(Ss[ty + 16][kk], q, acc1);
+      const float4 s0 = *reinterpret_cast<const float4*>(&Ss[kk][tr * 8]);
+      const float4 s1 = *reinterpret_cast<const float4*>(&Ss[kk][tr * 8 + 4]);
+      const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const float q = Qs[kk][tc + 16 * g];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) acc[a][g] = fmaf(sv[a], q, acc[a][g]);
+      }
     }
     __syncthreads();
   }
-  int gc = c0 + tx;
-  if (gc < k) {
-    if (r0 + ty < n) W[(size_t)gc * ldw + r0 + ty] = acc0;
-    if (r0 + ty + 16 < n) W[(size_t)gc * ldw + r0 + ty + 16] = acc1;
+  const int nsl = gridDim.y;
+  if (nsl == 1) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int col = tc + 16 * g;
+      if (col < kc)
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int row = r0 + tr * 8 + a;
+          if (row < n) W[(size_t)(c0 + col) * ldw + row] = acc[a][g];
+        }
+    }
+    return;
   }
+  // slice partials: part[(tile * nsl + slice) * 128 * 64 + col * 128 + row]
+  const int tile = blockIdx.z * gridDim.x + blockIdx.x;
+  float* my = part + ((size_t)tile * nsl + blockIdx.y) * (MV_RB * 64);
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) my[(tc + 16 * g) * MV_RB + tr * 8 + a] = acc[a][g];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(&counters[tile], 1u) == (unsigned)(nsl - 1));
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const float* base = part + (size_t)tile * nsl * (MV_RB * 64);
+  for (int idx = tid; idx < kc * MV_RB; idx += 256) {
+    const int col = idx / MV_RB, rr = idx % MV_RB;
+    const int row = r0 + rr;
+    float sum = 0.f;
+    for (int sl = 0; sl < nsl; ++sl) sum += __ldcg(&base[(size_t)sl * (MV_RB * 64) + col * MV_RB + rr]);
+    if (row < n) W[(size_t)(c0 + col) * ldw + row] = sum;
+  }
+  if (tid == 0) counters[tile] = 0u;
 }
 
+// Number of inner-dimension slices for an n x n product with `k` columns.
+static int matvec_slices(int n, int k) {
+  const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
+  int ns = (2 * 148 + tiles - 1) / tiles;          // about two CTAs per SM
+  const int max_ns = (n + 4 * MV_KC - 1) / (4 * MV_KC);  // at least 4 chunks per slice
+  ns = std::max(1, std::min(ns, std::min(max_ns, 32)));
+  return ns;
+}
+
+size_t block_matvec_scratch_floats(int n, int k) {
+  const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
+  return (size_t)tiles * matvec_slices(n, k) * MV_RB * 64;
+}
+
+size_t block_matvec_counters(int n, int k) { return (size_t)((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64); }
+
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st, cudaGraphConditionalHandle cond,
-                         int set_cond) {
-  dim3 grid((n + MV_RB - 1) / MV_RB, (k + MV_CB - 1) / MV_CB);
-  k_block_matvec<<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, skip, cond, set_cond);
+                         int k, const int* skip, cudaStream_t st, float* part, unsigned* counters,
+                         cudaGraphConditionalHandle cond, int set_cond) {
+  int ns = part ? matvec_slices(n, k) : 1;
+  int kslice = ((n + ns - 1) / ns + MV_KC - 1) / MV_KC * MV_KC;
+  ns = (n + kslice - 1) / kslice;
+  dim3 grid((n + MV_RB - 1) / MV_RB, ns, (k + 63) / 64);
+  const int kmax = std::min(k, 64);
+  if (kmax <= 16)
+    k_block_matvec<1><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
+  else if (kmax <= 32)
+    k_block_matvec<2><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
+  else if (kmax <= 48)
+    k_block_matvec<3><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
+  else
+    k_block_matvec<4><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -239,94 +320,107 @@ void launch_block_update(float* Z, int ldz, int kb, const float* A, int lda, int
 // ---------------------------------------------------------------------------
 // Cholesky of the w x w Gram (FP64, one CTA) with deficient-column detection
 // ---------------------------------------------------------------------------
-// Writes the upper factor R (G = R^T R) as FP32 into Rout (w x w row-major,
-// diagonal stored as 1/R_jj) and flags[j] = 1 for columns whose remaining
-// norm fell below 1e-10 of their original norm (numerically dependent).
+// G = R^T R with R upper triangular; writes R^{-1} (FP32, w x w row-major,
+// upper triangular) and flags[j] = 1 for columns whose remaining norm fell
+// below 1e-10 of their original norm (numerically dependent; their row of R
+// is taken as e_j).  One barrier per elimination step: the factor is written
+// to a separate array so the trailing update reads stay race-free.
 __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int w,
-                                              float* __restrict__ Rout, int* __restrict__ flags,
+                                              float* __restrict__ Rinv_out, int* __restrict__ flags,
                                               const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ double Gs[kMaxW][kMaxW + 1];
+  extern __shared__ double chs[];
+  double(*Gs)[kMaxW + 1] = reinterpret_cast<double(*)[kMaxW + 1]>(chs);
+  double(*Rs)[kMaxW + 1] = reinterpret_cast<double(*)[kMaxW + 1]>(chs + kMaxW * (kMaxW + 1));
   __shared__ double d0[kMaxW];
   __shared__ int fl[kMaxW];
   const int tid = threadIdx.x;
   for (int idx = tid; idx < w * w; idx += blockDim.x) {
     int i = idx / w, j = idx % w;
     Gs[i][j] = 0.5 * (G[i * w + j] + G[j * w + i]);
+    Rs[i][j] = 0.0;
   }
   __syncthreads();
-  for (int j = tid; j < w; j += blockDim.x) {
-    d0[j] = Gs[j][j];
-    fl[j] = 0;
-  }
+  for (int j = tid; j < w; j += blockDim.x) d0[j] = Gs[j][j];
   __syncthreads();
   for (int j = 0; j < w; ++j) {
-    if (tid == 0) {
-      double piv = Gs[j][j];
-      if (!(piv > 1e-10 * d0[j]) || !(d0[j] > 0.0)) {
-        fl[j] = 1;
-        Gs[j][j] = 1.0;
-      } else {
-        Gs[j][j] = sqrt(piv);
-      }
-    }
-    __syncthreads();
-    const double djj = Gs[j][j];
-    const int def = fl[j];
-    for (int l = j + 1 + tid; l < w; l += blockDim.x) Gs[j][l] = def ? 0.0 : Gs[j][l] / djj;
-    __syncthreads();
+    const double piv = Gs[j][j];
+    const bool def = !(piv > 1e-10 * d0[j]) || !(d0[j] > 0.0);
+    const double djj = def ? 1.0 : sqrt(piv);
+    const double inv = 1.0 / djj;
     const int rem = w - j - 1;
-    for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
-      int k = j + 1 + idx / rem, l = j + 1 + idx % rem;
-      if (l >= k) Gs[k][l] -= Gs[j][k] * Gs[j][l];
+    if (tid == 0) {
+      Rs[j][j] = djj;
+      fl[j] = def ? 1 : 0;
     }
+    for (int l = j + 1 + tid; l < w; l += blockDim.x) Rs[j][l] = def ? 0.0 : Gs[j][l] * inv;
+    if (!def)
+      for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
+        int k = j + 1 + idx / rem, l = j + 1 + idx % rem;
+        if (l >= k) Gs[k][l] -= (Gs[j][k] * inv) * (Gs[j][l] * inv);
+      }
     __syncthreads();
-  }
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    int i = idx / w, j = idx % w;
-    float v = 0.f;
-    if (i == j) v = (float)(1.0 / Gs[i][i]);
-    else if (j > i) v = (float)Gs[i][j];
-    Rout[idx] = v;
   }
   for (int j = tid; j < w; j += blockDim.x) flags[j] = fl[j];
+  // R^{-1} by columns (thread j solves R x = e_j), staged in the upper part of Gs (free now)
+  for (int j = tid; j < w; j += blockDim.x) {
+    for (int i = j; i >= 0; --i) {
+      double sacc = (i == j) ? 1.0 : 0.0;
+      for (int k = i + 1; k <= j; ++k) sacc -= Rs[i][k] * Gs[k][j];
+      Gs[i][j] = sacc / Rs[i][i];
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    int i = idx / w, j = idx % w;
+    Rinv_out[idx] = (j >= i) ? (float)Gs[i][j] : 0.f;
+  }
 }
+
+constexpr size_t kCholSmem = 2 * (size_t)kMaxW * (kMaxW + 1) * sizeof(double);
 
 void launch_chol_inv(const double* G, int w, float* Rinv, int* flags, const int* skip, cudaStream_t st) {
-  k_chol<<<1, 256, 0, st>>>(G, w, Rinv, flags, skip);
+  k_chol<<<1, 256, kCholSmem, st>>>(G, w, Rinv, flags, skip);
 }
 
-// Z <- Z R^{-1} by forward substitution on each row (x R = z); flagged columns
-// are replaced by pseudo-random entries (re-orthogonalised by the caller).
+// Z <- Z R^{-1} row by row (R^{-1} upper triangular); flagged columns are
+// replaced by pseudo-random entries (re-orthogonalised by the caller).
+template <int WMAX>
 __global__ void __launch_bounds__(128) k_apply_rinv(float* __restrict__ Z, int ldz, int w,
-                                                    const float* __restrict__ R, const int* flags,
+                                                    const float* __restrict__ Ri, const int* flags,
                                                     int n, unsigned long long seed, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
-  __shared__ float Rs[kMaxW * kMaxW];
-  __shared__ int fl[kMaxW];
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) Rs[idx] = R[idx];
-  for (int j = threadIdx.x; j < w; j += blockDim.x) fl[j] = flags[j];
+  __shared__ float Rs[WMAX * WMAX];
+  __shared__ int fl[WMAX];
+  for (int idx = threadIdx.x; idx < WMAX * WMAX; idx += blockDim.x) {
+    int i = idx / WMAX, j = idx % WMAX;
+    Rs[idx] = (i < w && j < w) ? Ri[i * w + j] : 0.f;
+  }
+  for (int j = threadIdx.x; j < WMAX; j += blockDim.x) fl[j] = (j < w) ? flags[j] : 0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float x[kMaxW];
+  float z[WMAX];
 #pragma unroll
-  for (int j = 0; j < kMaxW; ++j) {
+  for (int k = 0; k < WMAX; ++k) z[k] = (k < w) ? Z[(size_t)k * ldz + i] : 0.f;
+#pragma unroll
+  for (int j = 0; j < WMAX; ++j) {
     if (j < w) {
-      float z = Z[(size_t)j * ldz + i];
-      for (int k = 0; k < j; ++k) z = fmaf(-x[k], Rs[k * w + j], z);
-      x[j] = fl[j] ? hash_uniform(seed, (unsigned long long)i, (unsigned long long)(1000 + j))
-                   : z * Rs[j * w + j];
+      float x = 0.f;
+#pragma unroll
+      for (int k = 0; k <= j; ++k) x = fmaf(z[k], Rs[k * WMAX + j], x);
+      if (fl[j]) x = hash_uniform(seed, (unsigned long long)i, (unsigned long long)(1000 + j));
+      Z[(size_t)j * ldz + i] = x;
     }
   }
-#pragma unroll
-  for (int j = 0; j < kMaxW; ++j)
-    if (j < w) Z[(size_t)j * ldz + i] = x[j];
 }
 
 void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* flags, int n,
                        unsigned long long seed, const int* skip, cudaStream_t st) {
-  k_apply_rinv<<<(n + 127) / 128, 128, 0, st>>>(Z, ldz, w, Rinv, flags, n, seed, skip);
+  const int blocks = (n + 127) / 128;
+  if (w <= 16) k_apply_rinv<16><<<blocks, 128, 0, st>>>(Z, ldz, w, Rinv, flags, n, seed, skip);
+  else if (w <= 32) k_apply_rinv<32><<<blocks, 128, 0, st>>>(Z, ldz, w, Rinv, flags, n, seed, skip);
+  else k_apply_rinv<64><<<blocks, 128, 0, st>>>(Z, ldz, w, Rinv, flags, n, seed, skip);
 }
 
 // ---------------------------------------------------------------------------
@@ -409,7 +503,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
         o2 += red[k];
         t2 += red[32 + k];
       }
-      s_stop = (o2 <= 1e-12 * t2) || (t2 == 0.0);
+      // the refinement below restores full accuracy, so the sweeps stop at
+      // off(A) <= 1e-5 ||A||_F (above the FP32 rounding floor of ~K eps ||A||)
+      s_stop = (o2 <= 1e-10 * t2) || (t2 == 0.0);
     }
     __syncthreads();
     if (s_stop) break;
@@ -447,12 +543,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
       __syncthreads();
       // A <- J^T A J: every 2x2 block (pair t rows, pair u columns) transforms
       // independently, B <- J_t^T B J_u; blocks t <= u, mirrored.
-      const int nblk = half * (half + 1) / 2;
-      for (int idx = tid; idx < nblk; idx += nth) {
-        int t = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
-        while (t * (t + 1) / 2 > idx) --t;
-        while ((t + 1) * (t + 2) / 2 <= idx) ++t;
-        const int u = idx - t * (t + 1) / 2;  // u <= t
+      for (int idx = tid; idx < half * half; idx += nth) {
+        const int t = idx / half, u = idx % half;
+        if (u > t) continue;
         const float ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
         if (st == 0.f && su == 0.f) continue;
         const int pt = pp[t], qt = qq[t], pu = pp[u], qu = qq[u];
@@ -620,6 +713,7 @@ static size_t jacobi_smem(int Kp) {
 
 void init_lanczos_attributes() {
   cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxK));
+  cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
 }
 
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,

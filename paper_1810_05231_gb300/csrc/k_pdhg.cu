@@ -53,6 +53,28 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
   return s_last != 0;
 }
 
+
+// out[i] = sum_{b < P} part[b * stride + i] for i < L, by all threads of the
+// block: groups of g threads (g a power of two, g <= 32, g * L <= blockDim)
+// share one output, thread j of a group adding blocks j, j+g, ... in order,
+// the group combining with a fixed shuffle tree (deterministic).
+__device__ void reduce_partials(const double* part, int P, int stride, int L, double* out) {
+  int g = 1;
+  while (g < 32 && 2 * g * L <= (int)blockDim.x) g *= 2;
+  const int per_pass = blockDim.x / g;
+  for (int i0 = 0; i0 < L; i0 += per_pass) {
+    const int i = i0 + (int)threadIdx.x / g, j = threadIdx.x % g;
+    double s = 0.0;
+    if (i < L) {
+#pragma unroll 4
+      for (int b = j; b < P; b += g) s += __ldcg(&part[(size_t)b * stride + i]);
+    }
+    for (int o = g / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, g);
+    if (i < L && j == 0) out[i] = s;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // Ritz vectors V = Q Y, S V = W Y, residuals and the projection's stop test
 // ---------------------------------------------------------------------------
@@ -119,7 +141,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     if (i < rows) wk.Vcm[(size_t)(nw * kMaxR + t) * wk.ldq + r0 + i] = Vs[i * (w + 1) + t];
   }
   // partial sums per Ritz column: ||wv - theta v||^2, v.wv, v.v, sum v
-  double* part = wk.ritz_part + (size_t)blockIdx.x * 4 * kMaxW;
+  double* part = wk.ritz_part + (size_t)blockIdx.x * 4 * w;
   for (int t = tid; t < w; t += blockDim.x) {
     double a = 0, b = 0, c = 0, d = 0;
     float tht = (float)th[t];
@@ -132,26 +154,20 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
       d += (double)v;
     }
     part[t] = a;
-    part[kMaxW + t] = b;
-    part[2 * kMaxW + t] = c;
-    part[3 * kMaxW + t] = d;
+    part[w + t] = b;
+    part[2 * w + t] = c;
+    part[3 * w + t] = d;
   }
   if (!last_block(&wk.counters[CNT_RITZ * 512])) return;
   // final reduction in block order
+  __shared__ double fin4[4 * kMaxW];
+  reduce_partials(wk.ritz_part, gridDim.x, 4 * w, 4 * w, fin4);
   __shared__ double fin[4 * kMaxW];
   for (int t = tid; t < w; t += blockDim.x) {
-    double a = 0, b = 0, c = 0, d = 0;
-    for (int bk = 0; bk < (int)gridDim.x; ++bk) {
-      const double* p = wk.ritz_part + (size_t)bk * 4 * kMaxW;
-      a += __ldcg(&p[t]);
-      b += __ldcg(&p[kMaxW + t]);
-      c += __ldcg(&p[2 * kMaxW + t]);
-      d += __ldcg(&p[3 * kMaxW + t]);
-    }
-    fin[t] = a;
-    fin[kMaxW + t] = b;
-    fin[2 * kMaxW + t] = c;
-    fin[3 * kMaxW + t] = d;
+    fin[t] = fin4[t];
+    fin[kMaxW + t] = fin4[w + t];
+    fin[2 * kMaxW + t] = fin4[2 * w + t];
+    fin[3 * kMaxW + t] = fin4[3 * w + t];
   }
   __syncthreads();
   if (tid == 0) {
@@ -264,12 +280,14 @@ __global__ void __launch_bounds__(256) k_mxdual(DevProblem pb, DevWork wk, int r
     dual_row(pb, wk, nw, od, row, mxn, r, lp, u);
   }
   block_sum<4>(u, sh);
+  __shared__ double tot[4];
+  __shared__ double pobj_s[1];
+  reduce_partials(wk.part, gridDim.x, 4, 3, tot);
+  // objective row m: tr(C X+)
+  reduce_partials(wk.chunk_part + pb.row_chunk[pb.m], pb.row_chunk[pb.m + 1] - pb.row_chunk[pb.m], 1, 1, pobj_s);
   if (threadIdx.x == 0) {
-    double s[3] = {u[0], u[1], u[2]};
-    for (int b = 0; b < (int)gridDim.x; ++b)
-      for (int k = 0; k < 3; ++k) s[k] += __ldcg(&wk.part[(size_t)b * 4 + k]);
-    double pobj = 0.0;  // objective row m: tr(C X+)
-    for (int c = pb.row_chunk[pb.m]; c < pb.row_chunk[pb.m + 1]; ++c) pobj += __ldcg(&wk.chunk_part[c]);
+    double s[3] = {u[0] + tot[0], u[1] + tot[1], u[2] + tot[2]};
+    const double pobj = pobj_s[0];
     wk.mx[nw][pb.m] = pobj;
     ctl->red_dual[0] = s[0];
     ctl->red_dual[1] = s[1];
@@ -304,12 +322,10 @@ __global__ void __launch_bounds__(256) k_dvals(DevProblem pb, DevWork wk) {
     part[1] = v[1];
   }
   if (!last_block(&wk.counters[CNT_DVALS * 512])) return;
+  __shared__ double tot2[2];
+  reduce_partials(wk.part, gridDim.x, 2, 2, tot2);
   if (threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      s0 += __ldcg(&wk.part[(size_t)b * 2]);
-      s1 += __ldcg(&wk.part[(size_t)b * 2 + 1]);
-    }
+    const double s0 = tot2[0], s1 = tot2[1];
     double sh0 = 0.0, sh1 = 0.0;
     for (int d = 0; d < pb.n_dense; ++d) {
       sh0 += pb.dense_a[d] * wk.y[pb.dense_row[d]];
@@ -338,8 +354,9 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
   const int ldg = 2 * kMaxR;
   const int on = nw * kMaxR, oo = od * kMaxR;
   double v[3] = {0.0, 0.0, 0.0};
-  for (int idx = threadIdx.x; idx < kMaxR * kMaxR; idx += blockDim.x) {
-    int s = idx / kMaxR, t = idx % kMaxR;
+  const int rm = max(r, ro);
+  for (int idx = threadIdx.x; idx < rm * rm; idx += blockDim.x) {
+    int s = idx / rm, t = idx % rm;
     if (s < r && t < r) {
       double g = G[(size_t)(on + s) * ldg + on + t];
       v[0] += fmax(wk.lam[nw][s], 0.0) * fmax(wk.lam[nw][t], 0.0) * g * g;

@@ -124,6 +124,8 @@ struct DevWork {
   unsigned* counters;          // last-block counters (512 per kernel kind)
   float* Vcm;                  // column-major factor slots [slot 0 | slot 1], kMaxR columns each
   double* Hx;                  // Gram of the factor slots (2 kMaxR)^2
+  float* mv_part;              // split-K partials of the block product
+  unsigned* mv_cnt;            // its per-tile counters
   Ctl* ctl;
 };
 
@@ -132,9 +134,16 @@ enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_NUM }
 // ---------------------------------------------------------------------------
 // launchers (k_lanczos.cu)
 // ---------------------------------------------------------------------------
+// W = S Q (S n x n symmetric, row stride lds; Q, W column-major).  With
+// `part` / `counters` (sizes from block_matvec_scratch_floats / _counters;
+// counters zeroed once, the kernel leaves them zeroed) the inner dimension is
+// split over about two CTAs per SM; without them one CTA per 128-row block.
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st,
-                         cudaGraphConditionalHandle cond = 0, int set_cond = 0);
+                         int k, const int* skip, cudaStream_t st, float* part = nullptr,
+                         unsigned* counters = nullptr, cudaGraphConditionalHandle cond = 0,
+                         int set_cond = 0);
+size_t block_matvec_scratch_floats(int n, int k);
+size_t block_matvec_counters(int n, int k);
 void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
                          cudaStream_t st);
 // H = A^T B (ka x kb, FP64 row-major) with deterministic block reduction.

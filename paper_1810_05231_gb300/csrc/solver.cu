@@ -204,6 +204,9 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   CKA(dalloc(allocs, &Hx, (size_t)4 * kMaxR * kMaxR));
   Wk.Vcm = Vcm;
   Wk.Hx = Hx;
+  CKA(dalloc(allocs, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxW)));
+  CKA(dalloc(allocs, &Wk.mv_cnt, block_matvec_counters(n, kMaxW)));
+  CK(cudaMemsetAsync(Wk.mv_cnt, 0, sizeof(unsigned) * block_matvec_counters(n, kMaxW), st));
   CK(cudaMemsetAsync(Wk.counters, 0, sizeof(unsigned) * CNT_NUM * 512, st));
   CK(cudaMemsetAsync(Wk.Q, 0, sizeof(float) * (size_t)ld * kMaxK, st));
   CK(cudaMemsetAsync(Wk.W, 0, sizeof(float) * (size_t)ld * kMaxK, st));
@@ -281,7 +284,7 @@ static void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
                      n, w, skip, st);
     enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st);
     launch_block_matvec(wk.S, wk.lds, n, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
-                        wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st);
+                        wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st, wk.mv_part, wk.mv_cnt);
     dbg(wk, "cycle matvec", st);
   }
   launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
@@ -304,7 +307,8 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   } else {
     g_debug_n = n;
     enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
-    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, inner, use);
+    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, wk.mv_part, wk.mv_cnt,
+                        inner, use);
     dbg(wk, "warm matvec", st);
     if (in_graph) {
       cudaStreamCaptureStatus cs;
@@ -713,7 +717,7 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
   } else {
     launch_random_block(wk.Q, wk.ldq, n, 0, w, sv.seed, sv.st);
     enqueue_orth(wk, n, 0, w, sv.seed, nullptr, sv.st);
-    launch_block_matvec(S, lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, w, nullptr, sv.st);
+    launch_block_matvec(S, lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, w, nullptr, sv.st, wk.mv_part, wk.mv_cnt);
     for (int cyc = 0; cyc < c.max_cycles; ++cyc)
       enqueue_cycle(wk, n, w, K, s, r, sv.seed + 1000ULL * (unsigned long long)(cyc + 1), 0, 0, sv.st);
   }

@@ -56,7 +56,7 @@ struct Solver {
   std::map<GraphKey, cudaGraphExec_t> graphs;
   int r = 8;
   int rank_changes = 0;
-  int k_target = 64;  // Rayleigh-Ritz basis size aimed at by dims()
+  int k_target = 32;  // Rayleigh-Ritz basis size aimed at by dims() (one Krylov step per cycle)
   unsigned long long seed = 1;
 
   ~Solver();
