@@ -14,6 +14,8 @@
 
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 namespace psdp {
 
 // ---------------------------------------------------------------------------
@@ -52,42 +54,50 @@ struct DF {
 };
 
 // ---------------------------------------------------------------------------
-// S * Q block product (SIMT, split over the inner dimension)
+// S * Q block product (SIMT, inner dimension split across a thread-block cluster)
 // ---------------------------------------------------------------------------
-// CTA tile: 128 rows of S x up to 64 columns of Q, over one slice [k0, k1) of
-// the inner dimension, in chunks of 32.  The S chunk is staged transposed
-// (Ss[k][row]) so a thread reads its 8 rows as two float4 broadcasts; each
-// thread accumulates 8 rows x G columns (G = column groups of 16).  Slices are
-// summed by the last CTA of each (row block, column block) in slice order
-// (deterministic).  S is symmetric, so its row blocks are also column blocks.
+// CTA tile: 128 rows of S x up to 64 columns of Q over one slice of the inner
+// dimension, in chunks of 32.  The S chunk is staged transposed (Ss[k][row])
+// so a thread reads its 8 rows as two float4 broadcasts; each thread holds
+// 8 rows x G columns (G = column groups of 16).  The `ns` slices of a row
+// block form one cluster: their partial tiles stay in shared memory and, after
+// a cluster barrier, CTA c of the cluster sums rows [c*128/ns, (c+1)*128/ns)
+// over the ns partials through distributed shared memory, in slice order
+// (deterministic, no global partials).  S is symmetric, so its row blocks are
+// also column blocks.
 constexpr int MV_RB = 128, MV_KC = 32, MV_LDS = 132;
 
 template <int G>
 __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ S, int lds, int n,
                                                       const float* __restrict__ Q, int ldq,
                                                       float* __restrict__ W, int ldw, int k,
-                                                      int kslice, float* __restrict__ part,
-                                                      unsigned* counters, const int* skip,
+                                                      int kslice, const int* skip,
                                                       cudaGraphConditionalHandle cond, int set_cond) {
-  if (skip && *(volatile const int*)skip) return;
+  namespace cg = cooperative_groups;
+  if (skip && *(volatile const int*)skip) return;  // uniform over the grid: no CTA reaches a barrier
   if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     cudaGraphSetConditional(cond, 1u);
-  __shared__ __align__(16) float Ss[MV_KC][MV_LDS];
-  __shared__ float Qs[MV_KC][16 * G + 1];
-  __shared__ unsigned s_last;
+  // staging (S chunk, Q chunk) and, after the main loop, this CTA's partial
+  // tile (column-major, 16G x 128) share one buffer
+  constexpr int kStage = MV_KC * MV_LDS + MV_KC * (16 * G + 1);
+  constexpr int kPart = 16 * G * MV_RB;
+  __shared__ __align__(16) float smbuf[kStage > kPart ? kStage : kPart];
+  float(*Ss)[MV_LDS] = reinterpret_cast<float(*)[MV_LDS]>(smbuf);
+  float(*Qs)[16 * G + 1] = reinterpret_cast<float(*)[16 * G + 1]>(smbuf + MV_KC * MV_LDS);
+  float(*Ps)[MV_RB] = reinterpret_cast<float(*)[MV_RB]>(smbuf);
   const int tid = threadIdx.x;
   const int tc = tid & 15, tr = tid >> 4;  // column within group, row group (8 rows)
-  const int r0 = blockIdx.x * MV_RB;
+  const int ns = gridDim.x;                // slices = cluster size
+  const int r0 = blockIdx.y * MV_RB;
   const int c0 = blockIdx.z * 64;
   const int kc = min(16 * G, k - c0);
-  const int kb = blockIdx.y * kslice, ke = min(n, kb + kslice);
+  const int kb = blockIdx.x * kslice, ke = min(n, kb + kslice);
   float acc[8][G];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[a][g] = 0.f;
   for (int k0 = kb; k0 < ke; k0 += MV_KC) {
-    // S chunk: 128 rows x 32 columns, coalesced along the row, stored transposed
     for (int idx = tid; idx < MV_RB * MV_KC; idx += 256) {
       int rr = idx / MV_KC, kk = idx % MV_KC;
       int gr = r0 + rr, gk = k0 + kk;
@@ -113,8 +123,7 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
     }
     __syncthreads();
   }
-  const int nsl = gridDim.y;
-  if (nsl == 1) {
+  if (ns == 1) {
 #pragma unroll
     for (int g = 0; g < G; ++g) {
       const int col = tc + 16 * g;
@@ -127,62 +136,71 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
     }
     return;
   }
-  // slice partials: part[(tile * nsl + slice) * 128 * 64 + col * 128 + row]
-  const int tile = blockIdx.z * gridDim.x + blockIdx.x;
-  float* my = part + ((size_t)tile * nsl + blockIdx.y) * (MV_RB * 64);
 #pragma unroll
   for (int g = 0; g < G; ++g)
 #pragma unroll
-    for (int a = 0; a < 8; ++a) my[(tc + 16 * g) * MV_RB + tr * 8 + a] = acc[a][g];
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&counters[tile], 1u) == (unsigned)(nsl - 1));
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const float* base = part + (size_t)tile * nsl * (MV_RB * 64);
-  for (int idx = tid; idx < kc * MV_RB; idx += 256) {
-    const int col = idx / MV_RB, rr = idx % MV_RB;
-    const int row = r0 + rr;
+    for (int a = 0; a < 8; ++a) Ps[tc + 16 * g][tr * 8 + a] = acc[a][g];
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  const int rank = (int)cluster.block_rank();
+  const int rows_per = MV_RB / ns;
+  for (int idx = tid; idx < kc * rows_per; idx += 256) {
+    const int col = idx / rows_per, rr = rank * rows_per + idx % rows_per;
     float sum = 0.f;
-    for (int sl = 0; sl < nsl; ++sl) sum += __ldcg(&base[(size_t)sl * (MV_RB * 64) + col * MV_RB + rr]);
+    for (int sl = 0; sl < ns; ++sl) {
+      const float* rp = cluster.map_shared_rank(&Ps[0][0], sl);
+      sum += rp[col * MV_RB + rr];
+    }
+    const int row = r0 + rr;
     if (row < n) W[(size_t)(c0 + col) * ldw + row] = sum;
   }
-  if (tid == 0) counters[tile] = 0u;
+  cluster.sync();  // keep every CTA's shared memory alive until all reads are done
 }
 
-// Number of inner-dimension slices for an n x n product with `k` columns.
+// Inner-dimension slices per 128-row block: a power of two <= 8 (the cluster
+// size), about two CTAs per SM, at least four 32-wide chunks per slice.
 static int matvec_slices(int n, int k) {
   const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
-  int ns = (2 * 148 + tiles - 1) / tiles;          // about two CTAs per SM
-  const int max_ns = (n + 4 * MV_KC - 1) / (4 * MV_KC);  // at least 4 chunks per slice
-  ns = std::max(1, std::min(ns, std::min(max_ns, 32)));
+  int ns = 1;
+  while (ns < 8 && tiles * ns * 2 <= 2 * 148 && (n + 2 * ns * 4 * MV_KC - 1) / (2 * ns * 4 * MV_KC) >= 1 &&
+         n >= 2 * ns * 4 * MV_KC)
+    ns *= 2;
   return ns;
 }
 
-size_t block_matvec_scratch_floats(int n, int k) {
-  const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
-  return (size_t)tiles * matvec_slices(n, k) * MV_RB * 64;
+size_t block_matvec_scratch_floats(int, int) { return 0; }
+size_t block_matvec_counters(int, int) { return 0; }
+
+template <int G>
+static void launch_mv(dim3 grid, int ns, cudaStream_t st, const float* S, int lds, int n, const float* Q,
+                      int ldq, float* W, int ldw, int k, int kslice, const int* skip,
+                      cudaGraphConditionalHandle cond, int set_cond) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ns;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_block_matvec<G>, S, lds, n, Q, ldq, W, ldw, k, kslice, skip, cond, set_cond);
 }
 
-size_t block_matvec_counters(int n, int k) { return (size_t)((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64); }
-
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st, float* part, unsigned* counters,
+                         int k, const int* skip, cudaStream_t st, float*, unsigned*,
                          cudaGraphConditionalHandle cond, int set_cond) {
-  int ns = part ? matvec_slices(n, k) : 1;
-  int kslice = ((n + ns - 1) / ns + MV_KC - 1) / MV_KC * MV_KC;
-  ns = (n + kslice - 1) / kslice;
-  dim3 grid((n + MV_RB - 1) / MV_RB, ns, (k + 63) / 64);
+  const int ns = matvec_slices(n, k);
+  const int kslice = ((n + ns - 1) / ns + MV_KC - 1) / MV_KC * MV_KC;
+  dim3 grid(ns, (n + MV_RB - 1) / MV_RB, (k + 63) / 64);
   const int kmax = std::min(k, 64);
-  if (kmax <= 16)
-    k_block_matvec<1><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
-  else if (kmax <= 32)
-    k_block_matvec<2><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
-  else if (kmax <= 48)
-    k_block_matvec<3><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
-  else
-    k_block_matvec<4><<<grid, 256, 0, st>>>(S, lds, n, Q, ldq, W, ldw, k, kslice, part, counters, skip, cond, set_cond);
+  if (kmax <= 16) launch_mv<1>(grid, ns, st, S, lds, n, Q, ldq, W, ldw, k, kslice, skip, cond, set_cond);
+  else if (kmax <= 32) launch_mv<2>(grid, ns, st, S, lds, n, Q, ldq, W, ldw, k, kslice, skip, cond, set_cond);
+  else if (kmax <= 48) launch_mv<3>(grid, ns, st, S, lds, n, Q, ldq, W, ldw, k, kslice, skip, cond, set_cond);
+  else launch_mv<4>(grid, ns, st, S, lds, n, Q, ldq, W, ldw, k, kslice, skip, cond, set_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -206,20 +224,22 @@ void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned lon
 // ---------------------------------------------------------------------------
 // Gram H = A^T B with exact-product accumulation
 // ---------------------------------------------------------------------------
-// Grid (tiles_a * tiles_b, nsplit).  Each CTA computes a 16 x 16 output tile
-// over one row range; the last CTA of each output tile adds the nsplit
-// partials in fixed order (deterministic).
+// Grid (output tiles, row splits); the row splits of one 16 x 16 output tile
+// form a thread-block cluster.  Each CTA accumulates its rows in FP32 pairs,
+// keeps its partial tile in shared memory, and after a cluster barrier CTA c
+// adds the partials of its share of the tile over the splits in split order
+// through distributed shared memory (deterministic).
 constexpr int GR_T = 16, GR_RC = 64;
 
 __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int lda, int ka,
                                               const float* __restrict__ B, int ldb, int kb, int n,
-                                              int rows_per_split, double* __restrict__ H,
-                                              double* __restrict__ part, unsigned* counters,
-                                              const int* skip, int act, int slot) {
-  if (skip && *(volatile const int*)skip) return;
+                                              int rows_per_split, double* __restrict__ H, const int* skip,
+                                              int act, int slot) {
+  namespace cg = cooperative_groups;
+  if (skip && *(volatile const int*)skip) return;  // uniform over the grid
   __shared__ float As[GR_RC][GR_T + 1];
   __shared__ float Bs[GR_RC][GR_T + 1];
-  __shared__ unsigned s_last;
+  __shared__ double Pt[GR_T * GR_T];
   const int tid = threadIdx.x;
   int a0, b0;
   if (act > 0) {
@@ -250,45 +270,48 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int l
     for (int i = 0; i < GR_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
     __syncthreads();
   }
-  // partials of this output tile: part[(tile * nsplit + split) * 256 + local]
-  double* my = part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (GR_T * GR_T);
-  my[tid] = acc.value();
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    unsigned prev = atomicAdd(&counters[blockIdx.x], 1u);
-    s_last = (prev == gridDim.y - 1);
+  const int ns = gridDim.y;
+  if (ns == 1) {
+    if (a0 + ty < ka && b0 + tx < kb) H[(size_t)(a0 + ty) * kb + b0 + tx] = acc.value();
+    return;
   }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int a = a0 + ty, b = b0 + tx;
-  if (a < ka && b < kb) {
-    double s = 0.0;
-    const double* base = part + (size_t)blockIdx.x * gridDim.y * (GR_T * GR_T);
-    for (int sp = 0; sp < (int)gridDim.y; ++sp) s += __ldcg(&base[(size_t)sp * (GR_T * GR_T) + tid]);
-    H[(size_t)a * kb + b] = s;
+  Pt[tid] = acc.value();
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  const int rank = (int)cluster.block_rank();
+  const int per_rank = (GR_T * GR_T) / ns;
+  for (int o = rank * per_rank + tid; o < (rank + 1) * per_rank && tid < per_rank; o += 256) {
+    double sum = 0.0;
+    for (int sp = 0; sp < ns; ++sp) sum += cluster.map_shared_rank(Pt, sp)[o];
+    const int a = a0 + o / GR_T, b = b0 + o % GR_T;
+    if (a < ka && b < kb) H[(size_t)a * kb + b] = sum;
   }
-  if (tid == 0) counters[blockIdx.x] = 0u;
+  cluster.sync();
 }
 
 void launch_gram(const float* A, int lda, int ka, const float* B, int ldb, int kb, int n, double* H,
-                 double* part, unsigned* counter, const int* skip, cudaStream_t st, int act,
-                 int slot) {
+                 double*, unsigned*, const int* skip, cudaStream_t st, int act, int slot) {
   int tiles = ((ka + GR_T - 1) / GR_T) * ((kb + GR_T - 1) / GR_T);
   if (act > 0) {
     int per = (act + GR_T - 1) / GR_T;
     tiles = per * (ka / slot) * per * (kb / slot);
   }
-  int nsplit = 148 / tiles;
-  if (nsplit < 1) nsplit = 1;
-  int rows = (n + nsplit - 1) / nsplit;
-  if (rows < 128) rows = 128;
-  nsplit = (n + rows - 1) / rows;
-  if (nsplit < 1) nsplit = 1;
-  dim3 grid(tiles, nsplit);
-  k_gram<<<grid, 256, 0, st>>>(A, lda, ka, B, ldb, kb, n, rows, H, part, counter, skip, act,
-                               slot > 0 ? slot : 1);
+  // row splits: a power of two <= 8, >= 256 rows each, about 148 CTAs in all
+  int ns = 1;
+  while (ns < 8 && tiles * ns * 2 <= 148 && n >= 2 * ns * 256) ns *= 2;
+  const int rows = (n + ns - 1) / ns;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles, ns, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = ns;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_gram, A, lda, ka, B, ldb, kb, n, rows, H, skip, act, slot > 0 ? slot : 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,16 +366,24 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
   __syncthreads();
   for (int j = tid; j < w; j += blockDim.x) d0[j] = Gs[j][j];
   __syncthreads();
+  __shared__ double s_inv;
+  __shared__ int s_def;
+  __shared__ double rdiag[kMaxW];
   for (int j = 0; j < w; ++j) {
-    const double piv = Gs[j][j];
-    const bool def = !(piv > 1e-10 * d0[j]) || !(d0[j] > 0.0);
-    const double djj = def ? 1.0 : sqrt(piv);
-    const double inv = 1.0 / djj;
-    const int rem = w - j - 1;
-    if (tid == 0) {
+    if (tid == 0) {  // one FP64 square root / division per step (FP64 specials are slow)
+      const double piv = Gs[j][j];
+      const bool def = !(piv > 1e-10 * d0[j]) || !(d0[j] > 0.0);
+      const double djj = def ? 1.0 : sqrt(piv);
+      s_inv = 1.0 / djj;
+      s_def = def ? 1 : 0;
       Rs[j][j] = djj;
-      fl[j] = def ? 1 : 0;
+      rdiag[j] = s_inv;
+      fl[j] = s_def;
     }
+    __syncthreads();
+    const double inv = s_inv;
+    const int def = s_def;
+    const int rem = w - j - 1;
     for (int l = j + 1 + tid; l < w; l += blockDim.x) Rs[j][l] = def ? 0.0 : Gs[j][l] * inv;
     if (!def)
       for (int idx = tid; idx < rem * rem; idx += blockDim.x) {
@@ -367,7 +398,7 @@ __global__ void __launch_bounds__(256) k_chol(const double* __restrict__ G, int 
     for (int i = j; i >= 0; --i) {
       double sacc = (i == j) ? 1.0 : 0.0;
       for (int k = i + 1; k <= j; ++k) sacc -= Rs[i][k] * Gs[k][j];
-      Gs[i][j] = sacc / Rs[i][i];
+      Gs[i][j] = sacc * rdiag[i];
     }
   }
   __syncthreads();
@@ -684,7 +715,8 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
     int i = o / nout, j = o % nout;
     if (j < i) continue;
     DF g;
-    for (int k = 0; k < K; ++k) g.fma_acc(Yout[(size_t)i * ldy + k], Yout[(size_t)j * ldy + k]);
+#pragma unroll 8
+    for (int k = 0; k < K; ++k) g.fma_acc(__ldcg(&Yout[(size_t)i * ldy + k]), __ldcg(&Yout[(size_t)j * ldy + k]));
     float v = (float)((i == j ? 1.0 : 0.0) - g.value());
     A[i * nout + j] = v;
     A[j * nout + i] = v;
@@ -693,8 +725,9 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
   for (int o = tid; o < K * nout; o += nth) {
     int row = o / nout, j = o % nout;
     float corr = 0.f;
-    for (int i = 0; i < nout; ++i) corr = fmaf(Yout[(size_t)i * ldy + row], A[i * nout + j], corr);
-    V[row * ld + j] = Yout[(size_t)j * ldy + row] + 0.5f * corr;
+#pragma unroll 8
+    for (int i = 0; i < nout; ++i) corr = fmaf(__ldcg(&Yout[(size_t)i * ldy + row]), A[i * nout + j], corr);
+    V[row * ld + j] = __ldcg(&Yout[(size_t)j * ldy + row]) + 0.5f * corr;
   }
   __syncthreads();
   for (int o = tid; o < K * nout; o += nth) {

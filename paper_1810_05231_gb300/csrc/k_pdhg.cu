@@ -9,6 +9,8 @@
 
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 namespace psdp {
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -466,8 +468,10 @@ struct DFc {
 
 __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk, int act, int rows_per_split,
                                                       cudaGraphConditionalHandle cond, int use_cond) {
+  namespace cg = cooperative_groups;
   __shared__ float As[GC_RC][GC_T + 1];
   __shared__ float Bs[GC_RC][GC_T + 1];
+  __shared__ double Pt[GC_T * GC_T];
   __shared__ unsigned s_last;
   const int tid = threadIdx.x;
   const int n = pb.n;
@@ -495,31 +499,29 @@ __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk,
     for (int i = 0; i < GC_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
     __syncthreads();
   }
-  double* part = wk.part + ((size_t)blockIdx.x * gridDim.y + blockIdx.y) * (GC_T * GC_T);
-  part[tid] = acc.value();
+  // reduce the row splits of this tile across the cluster (split order)
+  Pt[tid] = acc.value();
+  cg::cluster_group cluster = cg::this_cluster();
+  cluster.sync();
+  const int ns = gridDim.y;
+  const int rank = (int)cluster.block_rank();
+  const int per_rank = (GC_T * GC_T) / ns;
+  if (tid < per_rank) {
+    const int o = rank * per_rank + tid;
+    double sum = 0.0;
+    for (int sp = 0; sp < ns; ++sp) sum += cluster.map_shared_rank(Pt, sp)[o];
+    wk.Hx[(size_t)(a0 + o / GC_T) * ka + b0 + o % GC_T] = sum;
+  }
+  cluster.sync();
+  // the last CTA to finish runs the controller
   unsigned* cnt = wk.counters + CNT_CTL * 512;
   __threadfence();
   __syncthreads();
-  if (tid == 0) s_last = (atomicAdd(&cnt[blockIdx.x], 1u) == gridDim.y - 1);
+  if (tid == 0) s_last = (atomicAdd(&cnt[0], 1u) == gridDim.x * gridDim.y - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  {
-    double s = 0.0;
-    const double* base = wk.part + (size_t)blockIdx.x * gridDim.y * (GC_T * GC_T);
-    for (int sp = 0; sp < (int)gridDim.y; ++sp) s += __ldcg(&base[(size_t)sp * (GC_T * GC_T) + tid]);
-    wk.Hx[(size_t)(a0 + ty) * ka + b0 + tx] = s;
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    cnt[blockIdx.x] = 0u;
-    s_last = (atomicAdd(&cnt[511], 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (tid == 0) cnt[511] = 0u;
+  if (tid == 0) cnt[0] = 0u;
   control_tail(pb, wk, wk.Hx, cond, use_cond);
 }
 
@@ -691,13 +693,21 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
   const int per = (act + GC_T - 1) / GC_T;
   const int tiles = per * 2 * per * 2;
-  int nsplit = 148 / tiles;
-  if (nsplit < 1) nsplit = 1;
-  int rows = (pb.n + nsplit - 1) / nsplit;
-  if (rows < 128) rows = 128;
-  nsplit = (pb.n + rows - 1) / rows;
-  if (nsplit < 1) nsplit = 1;
-  k_gram_control<<<dim3(tiles, nsplit), 256, 0, st>>>(pb, wk, act, rows, cond, use_cond);
+  int ns = 1;
+  while (ns < 8 && tiles * ns * 2 <= 148 && pb.n >= 2 * ns * 256) ns *= 2;
+  const int rows = (pb.n + ns - 1) / ns;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles, ns, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = ns;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_gram_control, pb, wk, act, rows, cond, use_cond);
 }
 
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st) {
