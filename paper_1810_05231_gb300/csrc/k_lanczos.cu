@@ -97,18 +97,80 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
   for (int a = 0; a < 8; ++a)
 #pragma unroll
     for (int g = 0; g < G; ++g) acc[a][g] = 0.f;
+  // Register staging: each thread loads 4 float4 of the S chunk (128 rows x 32
+  // columns) and G/2 (rounded up) float4 of the Q chunk, all issued before any
+  // is used, and the next chunk's loads are issued before the current chunk
+  // is consumed (software pipelining).  Rows of S and columns of Q are read
+  // with the inner index contiguous (coalesced 128-byte rows).
+  const bool vec = ((lds & 3) == 0) && ((ldq & 3) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(S) & 15) == 0) && ((reinterpret_cast<uintptr_t>(Q) & 15) == 0);
+  constexpr int QV = (16 * G * MV_KC / 4 + 255) / 256;  // float4 of Q per thread
+  float4 sreg[4], qreg[QV];
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int idx = tid + 256 * v;  // 1024 float4 = 128 rows x 8
+      const int rr = idx >> 3, kq = (idx & 7) * 4;
+      const int gr = r0 + rr, gk = k0 + kq;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gr < n) {
+        const float* src = S + (size_t)gr * lds + gk;
+        if (vec && gk + 3 < ke) x = __ldg(reinterpret_cast<const float4*>(src));
+        else {
+          if (gk < ke) x.x = __ldg(src);
+          if (gk + 1 < ke) x.y = __ldg(src + 1);
+          if (gk + 2 < ke) x.z = __ldg(src + 2);
+          if (gk + 3 < ke) x.w = __ldg(src + 3);
+        }
+      }
+      sreg[v] = x;
+    }
+#pragma unroll
+    for (int v = 0; v < QV; ++v) {
+      const int idx = tid + 256 * v;  // 16G columns x 8 float4
+      const int cc = idx >> 3, kq = (idx & 7) * 4;
+      const int gk = k0 + kq;
+      float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (cc < kc) {
+        const float* src = Q + (size_t)(c0 + cc) * ldq + gk;
+        if (vec && gk + 3 < ke) x = __ldg(reinterpret_cast<const float4*>(src));
+        else {
+          if (gk < ke) x.x = __ldg(src);
+          if (gk + 1 < ke) x.y = __ldg(src + 1);
+          if (gk + 2 < ke) x.z = __ldg(src + 2);
+          if (gk + 3 < ke) x.w = __ldg(src + 3);
+        }
+      }
+      qreg[v] = x;
+    }
+  };
+  auto store_chunk = [&]() {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int idx = tid + 256 * v;
+      const int rr = idx >> 3, kq = (idx & 7) * 4;
+      Ss[kq][rr] = sreg[v].x;
+      Ss[kq + 1][rr] = sreg[v].y;
+      Ss[kq + 2][rr] = sreg[v].z;
+      Ss[kq + 3][rr] = sreg[v].w;
+    }
+#pragma unroll
+    for (int v = 0; v < QV; ++v) {
+      const int idx = tid + 256 * v;
+      const int cc = idx >> 3, kq = (idx & 7) * 4;
+      if (cc < 16 * G) {
+        Qs[kq][cc] = qreg[v].x;
+        Qs[kq + 1][cc] = qreg[v].y;
+        Qs[kq + 2][cc] = qreg[v].z;
+        Qs[kq + 3][cc] = qreg[v].w;
+      }
+    }
+  };
+  if (kb < ke) load_chunk(kb);
   for (int k0 = kb; k0 < ke; k0 += MV_KC) {
-    for (int idx = tid; idx < MV_RB * MV_KC; idx += 256) {
-      int rr = idx / MV_KC, kk = idx % MV_KC;
-      int gr = r0 + rr, gk = k0 + kk;
-      Ss[kk][rr] = (gr < n && gk < ke) ? __ldg(&S[(size_t)gr * lds + gk]) : 0.f;
-    }
-    for (int idx = tid; idx < MV_KC * 16 * G; idx += 256) {
-      int cc = idx / MV_KC, kk = idx % MV_KC;
-      int gk = k0 + kk;
-      Qs[kk][cc] = (cc < kc && gk < ke) ? __ldg(&Q[(size_t)(c0 + cc) * ldq + gk]) : 0.f;
-    }
+    store_chunk();
     __syncthreads();
+    if (k0 + MV_KC < ke) load_chunk(k0 + MV_KC);  // in flight during the compute below
 #pragma unroll 4
     for (int kk = 0; kk < MV_KC; ++kk) {
       const float4 s0 = *reinterpret_cast<const float4*>(&Ss[kk][tr * 8]);
@@ -229,7 +291,7 @@ void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned lon
 // keeps its partial tile in shared memory, and after a cluster barrier CTA c
 // adds the partials of its share of the tile over the splits in split order
 // through distributed shared memory (deterministic).
-constexpr int GR_T = 16, GR_RC = 64;
+constexpr int GR_T = 16, GR_RC = 128;
 
 __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int lda, int ka,
                                               const float* __restrict__ B, int ldb, int kb, int n,
@@ -258,14 +320,31 @@ __global__ void __launch_bounds__(256) k_gram(const float* __restrict__ A, int l
   const int rbeg = blockIdx.y * rows_per_split;
   const int rend = min(n, rbeg + rows_per_split);
   DF acc;
+  // register staging with one chunk of prefetch: each thread issues its
+  // GR_RC * 16 / 256 loads of A and of B before the previous chunk is consumed
+  constexpr int NL = GR_RC * GR_T / 256;
+  float ra[NL], rb[NL];
+  auto load_chunk = [&](int i0) {
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      const int idx = tid + 256 * v;
+      const int c = idx / GR_RC, i = idx % GR_RC;
+      const int gi = i0 + i;
+      ra[v] = (gi < rend && a0 + c < ka) ? __ldg(&A[(size_t)(a0 + c) * lda + gi]) : 0.f;
+      rb[v] = (gi < rend && b0 + c < kb) ? __ldg(&B[(size_t)(b0 + c) * ldb + gi]) : 0.f;
+    }
+  };
+  if (rbeg < rend) load_chunk(rbeg);
   for (int i0 = rbeg; i0 < rend; i0 += GR_RC) {
-    for (int idx = tid; idx < GR_RC * GR_T; idx += 256) {
-      int c = idx / GR_RC, i = idx % GR_RC;
-      int gi = i0 + i;
-      As[i][c] = (gi < rend && a0 + c < ka) ? A[(size_t)(a0 + c) * lda + gi] : 0.f;
-      Bs[i][c] = (gi < rend && b0 + c < kb) ? B[(size_t)(b0 + c) * ldb + gi] : 0.f;
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      const int idx = tid + 256 * v;
+      const int c = idx / GR_RC, i = idx % GR_RC;
+      As[i][c] = ra[v];
+      Bs[i][c] = rb[v];
     }
     __syncthreads();
+    if (i0 + GR_RC < rend) load_chunk(i0 + GR_RC);
 #pragma unroll 8
     for (int i = 0; i < GR_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
     __syncthreads();
@@ -329,7 +408,8 @@ __global__ void __launch_bounds__(256) k_block_update(float* __restrict__ Z, int
   const int b = blockIdx.y;
   if (i >= n) return;
   float acc = 0.f;
-  for (int a = 0; a < ka; ++a) acc = fmaf(A[(size_t)a * lda + i], Hs[a * kb + b], acc);
+#pragma unroll 8
+  for (int a = 0; a < ka; ++a) acc = fmaf(__ldg(&A[(size_t)a * lda + i]), Hs[a * kb + b], acc);
   Z[(size_t)b * ldz + i] -= acc;
 }
 
@@ -628,12 +708,19 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
     rank[i] = rk;
   }
   __syncthreads();
-  // T (symmetrised, FP64) as a packed upper triangle in the freed A region
-  // (Kp (Kp+1)/2 doubles = Kp (Kp+1) floats)
-  double* Tp = reinterpret_cast<double*>(A);
+  // T (symmetrised) as a packed upper triangle in the freed A region, split
+  // once into FP32 hi + lo parts (Kp (Kp+1)/2 entries each = Kp (Kp+1) floats);
+  // hi + lo carries ~48 bits, enough for the FP32-pair products below
+  float* Th = A;
+  float* Tl = A + Kp * (Kp + 1) / 2;
   for (int idx = tid; idx < K * K; idx += nth) {
     int i = idx / K, j = idx % K;
-    if (i <= j) Tp[j * (j + 1) / 2 + i] = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
+    if (i <= j) {
+      const double t = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
+      const float hi = (float)t;
+      Th[j * (j + 1) / 2 + i] = hi;
+      Tl[j * (j + 1) / 2 + i] = (float)(t - (double)hi);
+    }
   }
   __syncthreads();
   // refinement scratch, per pass: Ph | Pl | Sm | Rm  (each Kp x jb floats)
@@ -655,12 +742,10 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
       const int j = wanted[jj];
       DF acc;
       for (int l = 0; l < K; ++l) {
-        double t = (k <= l) ? Tp[l * (l + 1) / 2 + k] : Tp[k * (k + 1) / 2 + l];
-        float hi = (float)t;
-        float lo = (float)(t - (double)hi);
-        float y = V[l * ld + j];
-        acc.fma_acc(hi, y);
-        acc.fma_acc(lo, y);
+        const int pi = (k <= l) ? l * (l + 1) / 2 + k : k * (k + 1) / 2 + l;
+        const float y = V[l * ld + j];
+        acc.fma_acc(Th[pi], y);
+        acc.fma_acc(Tl[pi], y);
       }
       Ph[k * jb + jj] = acc.hi;
       Pl[k * jb + jj] = acc.lo;
@@ -752,7 +837,9 @@ void init_lanczos_attributes() {
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
                     const int* skip, cudaStream_t st) {
   int Kp = (K + 1) & ~1;
-  k_jacobi<<<1, 512, jacobi_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
+  // fewer warps for small K: the rotation rounds are barrier-bound
+  const int threads = Kp <= 32 ? 128 : (Kp <= 64 ? 256 : 512);
+  k_jacobi<<<1, threads, jacobi_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
 }
 
 }  // namespace psdp

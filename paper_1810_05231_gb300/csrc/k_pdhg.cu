@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   const int r0 = blockIdx.x * RZ_RB;
   const int rows = min(RZ_RB, n - r0);
   const int nw = 1 - ctl->par;  // buffer of the new iterate
+#pragma unroll 4
   for (int idx = tid; idx < RZ_RB * K; idx += blockDim.x) {
     int k = idx / RZ_RB, i = idx % RZ_RB;
     float q = 0.f, ww = 0.f;
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     Qs[i * ldk + k] = q;
     Ws[i * ldk + k] = ww;
   }
+#pragma unroll 4
   for (int idx = tid; idx < K * w; idx += blockDim.x) {
     int t = idx / K, k = idx % K;
     Ys[k * w + t] = wk.Y[(size_t)t * kMaxK + k];
@@ -449,7 +451,7 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
 // Gram of the factor slots (only the first `act` columns of each slot; the
 // deterministic split-row reduction of the Lanczos Gram kernel) followed, in
 // the last block to finish, by the controller.
-constexpr int GC_T = 16, GC_RC = 64;
+constexpr int GC_T = 16, GC_RC = 128;
 
 struct DFc {
   float hi, lo;
@@ -487,14 +489,29 @@ __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk,
   const float* A = wk.Vcm;
   const int lda = wk.ldq;
   DFc acc;
+  constexpr int NL = GC_RC * GC_T / 256;
+  float ra[NL], rb[NL];
+  auto load_chunk = [&](int i0) {
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      const int idx = tid + 256 * v;
+      const int c = idx / GC_RC, i = idx % GC_RC;
+      const int gi = i0 + i;
+      ra[v] = (gi < rend) ? __ldg(&A[(size_t)(a0 + c) * lda + gi]) : 0.f;
+      rb[v] = (gi < rend) ? __ldg(&A[(size_t)(b0 + c) * lda + gi]) : 0.f;
+    }
+  };
+  if (rbeg < rend) load_chunk(rbeg);
   for (int i0 = rbeg; i0 < rend; i0 += GC_RC) {
-    for (int idx = tid; idx < GC_RC * GC_T; idx += 256) {
-      int c = idx / GC_RC, i = idx % GC_RC;
-      int gi = i0 + i;
-      As[i][c] = (gi < rend) ? A[(size_t)(a0 + c) * lda + gi] : 0.f;
-      Bs[i][c] = (gi < rend) ? A[(size_t)(b0 + c) * lda + gi] : 0.f;
+#pragma unroll
+    for (int v = 0; v < NL; ++v) {
+      const int idx = tid + 256 * v;
+      const int c = idx / GC_RC, i = idx % GC_RC;
+      As[i][c] = ra[v];
+      Bs[i][c] = rb[v];
     }
     __syncthreads();
+    if (i0 + GC_RC < rend) load_chunk(i0 + GC_RC);
 #pragma unroll 8
     for (int i = 0; i < GC_RC; ++i) acc.fma_acc(As[i][ty], Bs[i][tx]);
     __syncthreads();
@@ -541,6 +558,7 @@ __global__ void __launch_bounds__(256) k_rebuild(DevProblem pb, DevWork wk, int 
   const int bi = blockIdx.y, bj = blockIdx.x;
   const int p0 = bi * kTile, q0 = bj * kTile;
   const int n = pb.n;
+#pragma unroll 4
   for (int idx = tid; idx < kTile * r; idx += blockDim.x) {
     int i = idx / r, t = idx % r;
     float lp = (float)fmax(lam[t], 0.0);
