@@ -202,6 +202,26 @@ int proxsdp_gpu_aproj(const float* S, int64_t n, int64_t lds, int r, float* P, i
                       float* V, double* lambda, const proxsdp_gpu_settings* settings,
                       void* cuda_stream, proxsdp_gpu_info* info);
 
+/* aproj(S, r) for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this entry point exists for callers such as code running
+ * while a CUDA graph is being captured, applications whose own pool allocator
+ * owns all GPU memory, and embedded or real-time hosts that must not allocate
+ * (or risk an allocation failure) while they run.  Same arguments, results,
+ * defaults and errors as proxsdp_gpu_aproj, but the work buffers live in one
+ * file-scope static device array of about 6.7 MB, which every GPU that loads
+ * the library holds until the process exits; nothing is allocated per call
+ * (no cudaMalloc/cudaFree, no allocating library routine).
+ * Limits: n <= 2048 (larger n returns PROXSDP_ERR_UNSUPPORTED with a message
+ * for proxsdp_gpu_last_error(NULL)); r as for proxsdp_gpu_aproj.
+ * The first call on a device looks up the array's device address on that
+ * device (make that first call before any stream capture).  All calls share
+ * the one array, so calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller; each call clears the
+ * parts that must start at zero and synchronises its stream before returning. */
+int proxsdp_gpu_aproj_noalloc(const float* S, int64_t n, int64_t lds, int r, float* P, int64_t ldp,
+                              float* V, double* lambda, const proxsdp_gpu_settings* settings,
+                              void* cuda_stream, proxsdp_gpu_info* info);
+
 /* Symmetric block product W = S * Q (the Lanczos matvec): S n x n FP32 with
  * row stride lds, Q n x k FP32 column-major (stride ldq >= n), W likewise
  * (stride ldw).  k <= 256. */

@@ -17,6 +17,7 @@ from ._binding import (  # noqa: F401
     Solver,
     analyze_problem,
     aproj,
+    aproj_noalloc,
     block_matvec,
     default_settings,
     lib,

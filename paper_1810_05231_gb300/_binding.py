@@ -43,6 +43,7 @@ EXPORTED = [
     "proxsdp_gpu_block_matvec",
     "proxsdp_gpu_sym_eig",
     "proxsdp_gpu_analyze_problem",
+    "proxsdp_gpu_aproj_noalloc",
 ]
 
 
@@ -125,6 +126,8 @@ def lib():
     L.proxsdp_gpu_aproj.argtypes = [vp, i64, i64, i32, vp, i64, vp, vp, ctypes.POINTER(Settings), vp,
                                     ctypes.POINTER(Info)]
     L.proxsdp_gpu_block_matvec.argtypes = [vp, i64, i64, vp, i64, i32, vp, i64, vp]
+    L.proxsdp_gpu_aproj_noalloc.argtypes = [vp, i64, i64, i32, vp, i64, vp, vp, ctypes.POINTER(Settings), vp,
+                                            ctypes.POINTER(Info)]
     L.proxsdp_gpu_sym_eig.argtypes = [vp, i32, vp, vp, vp]
     L.proxsdp_gpu_analyze_problem.argtypes = [ctypes.POINTER(Settings), i64, dp, i64, dp, dp, i64, i64, dp, dp, dp,
                                               dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -285,6 +288,31 @@ def aproj(S, r, want_P=True, want_V=True, settings: Settings | None = None, stre
                                    _torch_stream(stream), ctypes.byref(info))
     _check(code)
     return P, (V.t() if V is not None else None), lam, info
+
+
+def aproj_noalloc(S, r, P=None, V=None, lam=None, settings: Settings | None = None, stream=None):
+    """aproj through proxsdp_gpu_aproj_noalloc (static device scratch, n <= 2048).
+
+    The outputs may be passed in (CUDA tensors: P n x n float32, V r x n
+    float32 = column-major n x r, lam r float64) so that the call itself
+    allocates nothing; missing ones are created here."""
+    import torch
+
+    assert S.is_cuda and S.dtype == torch.float32 and S.dim() == 2
+    n = S.shape[0]
+    if P is None:
+        P = torch.empty((n, n), device=S.device, dtype=torch.float32)
+    if V is None:
+        V = torch.empty((r, n), device=S.device, dtype=torch.float32)
+    if lam is None:
+        lam = torch.empty(r, device=S.device, dtype=torch.float64)
+    info = Info()
+    _check(lib().proxsdp_gpu_aproj_noalloc(ctypes.c_void_p(S.data_ptr()), n, S.stride(0), int(r),
+                                           ctypes.c_void_p(P.data_ptr()), P.stride(0),
+                                           ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                           ctypes.byref(settings) if settings is not None else None,
+                                           _torch_stream(stream), ctypes.byref(info)))
+    return P, V.t(), lam, info
 
 
 def block_matvec(S, Q, stream=None):

@@ -18,6 +18,11 @@ struct proxsdp_gpu_ctx {
 
 static std::string g_last_create_error;
 
+namespace psdp {
+// Error text for entry points that have no handle (read with proxsdp_gpu_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_last_create_error = msg; }
+}  // namespace psdp
+
 namespace {
 
 bool finite(double v) { return std::isfinite(v); }

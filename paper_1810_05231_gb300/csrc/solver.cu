@@ -245,8 +245,8 @@ int Solver::set_ctl_fields(int status, int it_stop, int rr, int w, int K, int k_
 // Orthonormalise Z = Q[:, c0:c0+w] against Q[:, :c0] and within itself:
 // two passes of (classical Gram-Schmidt, Cholesky QR); columns found
 // dependent in the first pass are refilled with pseudo-random vectors.
-static void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed,
-                         const int* skip, cudaStream_t st) {
+void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed,
+                  const int* skip, cudaStream_t st) {
   float* Z = wk.Q + (size_t)c0 * wk.ldq;
   unsigned* cnt = wk.counters + CNT_GRAM * 512;
   for (int pass = 0; pass < 2; ++pass) {
@@ -275,9 +275,9 @@ static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned lon
   launch_apply_rinv(Z, wk.ldq, w, wk.Hf, wk.flags, n, seed, nullptr, st);
 }
 
-static void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
-                          unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
-                          cudaStream_t st) {
+void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
+                   unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
+                   cudaStream_t st) {
   const int* skip = &wk.ctl->lz_done;
   for (int j = 1; j <= s; ++j) {
     launch_copy_cols(wk.W + (size_t)(j - 1) * w * wk.ldq, wk.ldq, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
