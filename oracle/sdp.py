@@ -374,7 +374,8 @@ def solve(prob_in: Problem, mode="lr", tol=1e-4, max_iter=100000, rank_init=8,
                 break
             r = min(2 * r, n, max_rank)
             k_change = it
-        elif it - k_change >= window and eps_comb >= eps_hist[it - 1 - window]:
+        elif it - k_change >= window and it - 1 - window >= 0 and eps_comb >= eps_hist[it - 1 - window]:
+            # eps^{k - l} exists only once l iterates precede k: before that no stall
             if not rank_ok:
                 if r >= max_rank:
                     status = STALLED_AT_MAX_RANK
