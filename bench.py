@@ -183,13 +183,17 @@ def run_ours(args, rank, world):
 
 
 def roofline(pkg, torch, stream, n, info):
-    """Time the dominant kernel alone (cold L2) and relate it to HBM bandwidth.
+    """Time the dominant HBM-bound kernel alone (cold L2) and relate it to HBM
+    bandwidth.
 
-    The block product S * Q (n x n FP32 S, n x 16 block) moves n^2 * 4 bytes
-    of S plus 2 * n * 16 * 4 bytes of Q and W per launch (algorithmic bytes).
+    The block product S * Q (n x n FP32 S, n x k block) moves n^2 * 4 bytes of
+    S plus 2 * n * k * 4 bytes of Q and W per launch (algorithmic bytes); k is
+    the Krylov block width the solve uses at its final rank r,
+    16 * ceil((r + max(8, r/4)) / 16).
     """
     hbm, _, src = _peaks()
-    k = 16
+    r = int(info["final_rank"])
+    k = min(64, 16 * ((r + max(8, r // 4) + 15) // 16))
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     S = torch.randn(n, n, device="cuda", generator=g)
@@ -215,12 +219,12 @@ def roofline(pkg, torch, stream, n, info):
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get("k_block_matvec_n2000_k16")
+            traffic = json.load(open(tp)).get(f"k_block_matvec_n{n}_k{k}")
         except Exception:
             traffic = None
     return {"kernel": "k_block_matvec", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-            "alg_bytes_per_launch": bytes_alg, "avg_launch_s": t, "l2": "flushed before each launch"}
+            "alg_bytes_per_launch": bytes_alg, "avg_launch_s": t, "k": k, "l2": "flushed before each launch"}
 
 
 def full_eig_baseline(torch, inst, stream, iters=10):

@@ -158,6 +158,21 @@ int proxsdp_gpu_analyze_problem(const proxsdp_gpu_settings* settings, int64_t n,
  * cap.  `info` may be NULL. */
 int proxsdp_gpu_solve(proxsdp_gpu_t h, proxsdp_gpu_info* info);
 
+/* Solve `count` independent problems concurrently on one GPU (many small
+ * instances of uneven size).  handles[i] is a handle created with its own
+ * stream (cuda_stream = NULL at create) and loaded with set_problem; all
+ * handles must be distinct.  `host_threads` host threads (<= 0: 16, at most
+ * `count`) each take the next unsolved handle, largest n first, and run
+ * proxsdp_gpu_solve on it, so the kernels and graphs of different handles run
+ * concurrently on their streams.  infos[i] (infos may be NULL) receives
+ * handle i's result.  Every handle is attempted; the return value is the
+ * first nonzero code in handle order (its message is on that handle), or
+ * PROXSDP_ERR_INVALID_ARG for a NULL/repeated handle (message on NULL).
+ * The CUDA_DEVICE_MAX_CONNECTIONS environment variable (set before the first
+ * CUDA call of the process) bounds how many streams run without false
+ * dependencies. */
+int proxsdp_gpu_solve_batch(proxsdp_gpu_t* handles, int count, proxsdp_gpu_info* infos, int host_threads);
+
 /* Copy the last iterate to the host.  Any pointer may be NULL.
  *   X      n*n doubles (dense V diag(max(lambda,0)) V^T),
  *   y      m_total doubles, the paper's dual sign, original row scaling,
@@ -193,8 +208,8 @@ const char* proxsdp_gpu_last_error(proxsdp_gpu_t h);
 /* Truncated psd projection aproj(S, r) of Sec. 3.1 (Eq. trunc_eig):
  * P = sum_{t<r} max(lambda_t, 0) v_t v_t^T over the r algebraically largest
  * eigenpairs of the symmetric S (n x n FP32, row stride lds >= n).  Computed
- * with the library's restarted block Lanczos (n > 128) or one-CTA Jacobi
- * (n <= 128).  Outputs (each may be NULL): P (n x n FP32, stride ldp), V
+ * with the library's restarted block Lanczos (n > 128) or the one-block dense
+ * eigensolver of proxsdp_gpu_sym_eig (n <= 128).  Outputs (each may be NULL): P (n x n FP32, stride ldp), V
  * (n x r FP32 column-major, stride n), lambda (r FP64, descending,
  * unclamped).  `settings` may be NULL.  `info` (may be NULL) receives
  * matvecs / lanczos_cycles / lanczos_unconverged / lambda_r. */
@@ -229,9 +244,13 @@ int proxsdp_gpu_block_matvec(const float* S, int64_t n, int64_t lds, const float
                              int k, float* W, int64_t ldw, void* cuda_stream);
 
 /* Eigendecomposition of a small symmetric matrix T (K x K FP64 row-major,
- * K <= 128) by cyclic Jacobi rotations in one thread block (the Rayleigh-Ritz
- * step of the Lanczos solver): theta (K FP64, descending) and Y (K x K FP32
- * column-major eigenvectors, column t for theta[t]). */
+ * K <= 128) in one thread block (the Rayleigh-Ritz step of the Lanczos
+ * solver): Householder reduction to tridiagonal form, Sturm-count bisection,
+ * inverse iteration (groups of close eigenvalues orthogonalised together),
+ * back-transformation, and one correction of every vector from residuals
+ * accumulated in FP32 pairs.  Outputs theta (K FP64, descending, Rayleigh
+ * quotients) and Y (K x K FP32 column-major eigenvectors, column t for
+ * theta[t]). */
 int proxsdp_gpu_sym_eig(const double* T, int K, double* theta, float* Y, void* cuda_stream);
 
 #ifdef __cplusplus

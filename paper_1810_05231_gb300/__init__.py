@@ -21,5 +21,6 @@ from ._binding import (  # noqa: F401
     block_matvec,
     default_settings,
     lib,
+    solve_batch,
     sym_eig,
 )

@@ -44,6 +44,7 @@ EXPORTED = [
     "proxsdp_gpu_sym_eig",
     "proxsdp_gpu_analyze_problem",
     "proxsdp_gpu_aproj_noalloc",
+    "proxsdp_gpu_solve_batch",
 ]
 
 
@@ -119,6 +120,7 @@ def lib():
     L.proxsdp_gpu_get_primal_dual.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
     L.proxsdp_gpu_set_iterate.argtypes = [vp, i32, dp, dp, dp]
     L.proxsdp_gpu_iterate.argtypes = [vp, i64, ctypes.POINTER(Info)]
+    L.proxsdp_gpu_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Info), i32]
     L.proxsdp_gpu_destroy.argtypes = [vp]
     L.proxsdp_gpu_destroy.restype = None
     L.proxsdp_gpu_last_error.argtypes = [vp]
@@ -245,6 +247,22 @@ class Solver:
         return dict(X=X, y=y[:m], V=V[: n * rr].reshape(rr, n).T.copy(), lam=lam[:rr].copy(), r=rr)
 
 
+def solve_batch(solvers, host_threads: int = 0):
+    """Solve the problems loaded in ``solvers`` (distinct ``Solver`` objects,
+    each on its own stream) concurrently; returns their ``Info`` in order."""
+    k = len(solvers)
+    hs = (ctypes.c_void_p * max(k, 1))(*[s.h for s in solvers])
+    infos = (Info * max(k, 1))()
+    code = lib().proxsdp_gpu_solve_batch(hs, k, infos, int(host_threads))
+    if code != OK:
+        msgs = [lib().proxsdp_gpu_last_error(s.h) for s in solvers if s.h]
+        msg = next((m.decode() for m in msgs if m), "")
+        if code == ERR_INVALID_ARG and not msg:
+            msg = (lib().proxsdp_gpu_last_error(None) or b"").decode()
+        raise ProxSDPError(code, msg)
+    return [infos[i] for i in range(k)]
+
+
 def analyze_problem(n, m_eq, A_rowptr, A_col, A_val, rhs, C_dense=None, C_idx=None, C_val=None,
                     settings: Settings | None = None):
     """Host-only validation and preprocessing (no GPU): returns
@@ -329,7 +347,7 @@ def block_matvec(S, Q, stream=None):
 
 
 def sym_eig(T, stream=None):
-    """Jacobi eigendecomposition of a CUDA float64 K x K symmetric tensor: (theta desc, Y columns)."""
+    """Eigendecomposition of a CUDA float64 K x K symmetric tensor (one thread block): (theta desc, Y columns)."""
     import torch
 
     K = T.shape[0]

@@ -1,10 +1,13 @@
 // api.cpp — the extern "C" boundary (include/proxsdp_gpu.h): argument
 // validation, the host-side layout passes of set_problem, and result export.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "solver.h"
@@ -559,6 +562,42 @@ int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V
   if (lambda)
     for (int t = 0; t < r; ++t) lambda[t] = lam[t];
   if (r_out) *r_out = r;
+  return PROXSDP_OK;
+}
+
+int proxsdp_gpu_solve_batch(proxsdp_gpu_t* handles, int count, proxsdp_gpu_info* infos, int host_threads) {
+  if (count < 0 || (count > 0 && !handles)) return PROXSDP_ERR_INVALID_ARG;
+  std::unordered_set<proxsdp_gpu_t> seen;
+  for (int i = 0; i < count; ++i) {
+    if (!handles[i] || !seen.insert(handles[i]).second) {
+      psdp::set_global_error("solve_batch: NULL or repeated handle");
+      return PROXSDP_ERR_INVALID_ARG;
+    }
+  }
+  // largest problems first (n^2 bounds the work of an iteration), so that the
+  // long solves start early and the short ones fill in behind them
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return handles[a]->s.hp.n > handles[b]->s.hp.n; });
+  std::vector<int> rc(count, PROXSDP_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = order[k];
+      rc[i] = proxsdp_gpu_solve(handles[i], infos ? &infos[i] : nullptr);
+    }
+  };
+  int nt = host_threads > 0 ? host_threads : 16;
+  nt = std::max(1, std::min(nt, count));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < count; ++i)
+    if (rc[i] != PROXSDP_OK) return rc[i];
   return PROXSDP_OK;
 }
 

@@ -6,8 +6,9 @@
 // column blocks, inner products are accumulated exactly-rounded in a pair of
 // FP32 numbers (Knuth's TwoSum with the FMA-based TwoProduct of Ogita, Rump &
 // Oishi, "Accurate sum and dot product", 2005) and combined across blocks in
-// FP64, and the small Rayleigh-Ritz eigenproblem is solved by cyclic Jacobi
-// rotations in one thread block.
+// FP64, and the small Rayleigh-Ritz eigenproblem is solved in one thread
+// block (Householder tridiagonalisation, bisection, inverse iteration and a
+// residual correction).
 #include "psdp.cuh"
 
 #include <math.h>
@@ -535,259 +536,588 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
 }
 
 // ---------------------------------------------------------------------------
-// Symmetric eigensolver: parallel cyclic Jacobi in one CTA + refinement
+// Symmetric eigensolver for the Rayleigh-Ritz matrix (one CTA, K <= 128)
 // ---------------------------------------------------------------------------
-// (1) Cyclic Jacobi in FP32.  Round-robin ordering: in round s (0..K-2)
-//     position K-1 meets s and, for t = 1..K/2-1, (s+t) mod (K-1) meets
-//     (s-t) mod (K-1); the K/2 rotations of a round act on disjoint pairs.
-//     Each rotation J (c, s in the (p,q) plane) zeroes A_pq
-//     (tan 2 theta = 2 A_pq / (A_qq - A_pp)); A <- J^T A J, V <- V J.
-//     Pairs with |A_pq| below 1e-7 sqrt(|A_pp A_qq|) are not rotated.  Sweeps
-//     stop when off(A) <= 1e-6 ||A||_F.
-// (2) One refinement step for the `nout` wanted eigenvectors (Ogita & Aishima,
+// (1) Householder reduction of T (FP32) to tridiagonal form: for k = 0..K-3
+//     the reflector H_k = I - tau_k v_k v_k^T (v_k(0) = 1, acting on rows
+//     k+1..K-1) annihilates column k below the subdiagonal, and the trailing
+//     block becomes A22 - v w^T - w v^T with p = tau A22 v and
+//     w = p - (tau/2)(p^T v) v.
+// (2) Eigenvalues of the tridiagonal matrix (scaled to unit infinity norm) by
+//     Sturm counts (the number of negative pivots of the LDL^T factorisation
+//     of T - x I): one count per thread at evenly spaced points of the
+//     Gershgorin interval brackets every eigenvalue, then G threads per
+//     eigenvalue narrow its bracket by multisection.
+// (3) Eigenvectors of the tridiagonal matrix by inverse iteration: three
+//     solves with the partially pivoted LU factorisation of T - lambda I from
+//     a pseudo-random start.  Eigenvalues closer than 1e-3 ||T|| form a group
+//     that one thread handles, orthogonalising each member against the
+//     previous ones after every solve (modified Gram-Schmidt).
+// (4) Back-transformation Y = H_0 H_1 ... H_{K-3} Z.
+// (5) One refinement step for the `nout` wanted eigenvectors (Ogita & Aishima,
 //     "Iterative refinement for symmetric eigenvalue decomposition", 2018):
-//     with Y the Jacobi vectors, S = Y^T T Y and R = I - Y^T Y accumulated in
+//     with Y the eigenvectors, S = Y^T T Y and R = I - Y^T Y accumulated in
 //     FP32 pairs against the FP64 input T, lambda_j = S_jj / (1 - R_jj) and
 //     y_j <- y_j + sum_i y_i E_ij,  E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i)
-//     (E_ij = R_ij / 2 for i = j or nearly equal eigenvalues).  The refined
-//     eigenvalues are FP64-accurate; the vectors are FP32-rounded.
+//     (E_ij = R_ij / 2 for i = j or nearly equal eigenvalues), followed by a
+//     symmetric orthonormality correction.
 constexpr int JB = 32;  // wanted columns refined per pass
+constexpr int SE_THREADS = 512;
+constexpr float kSePivmin = 1e-30f;   // Sturm pivots below this (unit-norm matrix) count as negative
+constexpr float kSeGroupTol = 1e-3f;  // inverse-iteration groups (unit-norm matrix)
 
-__global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, int K, int Kp,
-                                                double* __restrict__ theta, float* __restrict__ Yout,
-                                                int ldy, int nout, const int* skip) {
+// Numbers of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal)
+// below x0 and below x1 (two interleaved Sturm sequences).
+__device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int K, float x0, float x1,
+                                             int& c0, int& c1) {
+  float q0 = d[0] - x0, q1 = d[0] - x1;
+  if (fabsf(q0) < kSePivmin) q0 = -kSePivmin;
+  if (fabsf(q1) < kSePivmin) q1 = -kSePivmin;
+  int n0 = (q0 < 0.f), n1 = (q1 < 0.f);
+  for (int i = 1; i < K; ++i) {
+    const float di = d[i], ei = e2[i - 1];
+    q0 = (di - x0) - __fdividef(ei, q0);
+    q1 = (di - x1) - __fdividef(ei, q1);
+    if (fabsf(q0) < kSePivmin) q0 = -kSePivmin;
+    if (fabsf(q1) < kSePivmin) q1 = -kSePivmin;
+    n0 += (q0 < 0.f);
+    n1 += (q1 < 0.f);
+  }
+  c0 = n0;
+  c1 = n1;
+}
+
+// Partially pivoted LU factorisation of the tridiagonal T - lam I (diagonal
+// d, off-diagonal e), rows eliminated top-down: U has two superdiagonals;
+// u0 holds the reciprocals of the pivots.
+struct TriLU {
+  float u0[kMaxK], u1[kMaxK], u2[kMaxK], l[kMaxK];
+  unsigned sw[kMaxK / 32];
+};
+
+__device__ void tri_lu(const float* d, const float* e, int K, float lam, float tiny, TriLU& f) {
+  float p0 = d[0] - lam, p1 = (K > 1) ? e[0] : 0.f;
+  for (int w = 0; w < kMaxK / 32; ++w) f.sw[w] = 0u;
+  for (int i = 0; i < K - 1; ++i) {
+    const float s0 = e[i], s1 = d[i + 1] - lam, s2 = (i + 2 < K) ? e[i + 1] : 0.f;
+    if (fabsf(p0) >= fabsf(s0)) {  // the current row is the pivot row
+      if (p0 == 0.f) p0 = tiny;
+      const float l = s0 / p0;
+      f.u0[i] = 1.f / p0;
+      f.u1[i] = p1;
+      f.u2[i] = 0.f;
+      f.l[i] = l;
+      p0 = s1 - l * p1;
+      p1 = s2;
+    } else {  // rows i and i+1 swap
+      const float l = p0 / s0;
+      f.u0[i] = 1.f / s0;
+      f.u1[i] = s1;
+      f.u2[i] = s2;
+      f.l[i] = l;
+      f.sw[i >> 5] |= 1u << (i & 31);
+      p0 = p1 - l * s1;
+      p1 = -l * s2;
+    }
+  }
+  f.u0[K - 1] = 1.f / ((p0 == 0.f) ? tiny : p0);
+}
+
+// x <- (T - lam I)^{-1} x for the factorisation above; x has stride ld.
+__device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
+  for (int i = 0; i < K - 1; ++i) {
+    float a = x[i * ld], b = x[(i + 1) * ld];
+    if ((f.sw[i >> 5] >> (i & 31)) & 1u) {
+      const float t = a;
+      a = b;
+      b = t;
+      x[i * ld] = a;
+    }
+    x[(i + 1) * ld] = b - f.l[i] * a;
+  }
+  float x2 = 0.f, x1 = x[(K - 1) * ld] * f.u0[K - 1];
+  x[(K - 1) * ld] = x1;
+  for (int i = K - 2; i >= 0; --i) {
+    const float xi = (x[i * ld] - f.u1[i] * x1 - f.u2[i] * x2) * f.u0[i];
+    x[i * ld] = xi;
+    x2 = x1;
+    x1 = xi;
+  }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Normalise column q of V (K entries, stride ld) with the whole warp; a zero
+// or non-finite column is refilled with pseudo-random entries first.
+__device__ void warp_normalise(float* V, int ld, int K, int q, int lane, unsigned long long salt) {
+  float mx = 0.f;
+  for (int i = lane; i < K; i += 32) mx = fmaxf(mx, fabsf(V[i * ld + q]));
+  mx = warp_max_f(mx);
+  if (!(mx > 0.f) || !(mx < 3e38f)) {
+    for (int i = lane; i < K; i += 32) V[i * ld + q] = hash_uniform(0xBADULL + salt, (unsigned long long)i, 78ULL);
+    mx = 1.f;
+  }
+  const float im = 1.f / mx;
+  float ss = 0.f;
+  for (int i = lane; i < K; i += 32) {
+    const float v = V[i * ld + q] * im;
+    ss = fmaf(v, v, ss);
+  }
+  ss = warp_sum_f(ss);
+  const float sc = im * rsqrtf(ss);
+  for (int i = lane; i < K; i += 32) V[i * ld + q] *= sc;
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict__ Tin, int K, int Kp,
+                                                        double* __restrict__ theta, float* __restrict__ Yout,
+                                                        int ldy, int nout, int refine, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
   extern __shared__ float smj[];
   const int ld = Kp + 1;
-  float* A = smj;                      // Kp x (Kp+1)
-  float* V = A + (size_t)Kp * ld;      // Kp x (Kp+1)
-  float* cs = V + (size_t)Kp * ld;     // Kp/2
-  float* sn = cs + Kp / 2;             // Kp/2
-  float* dg = sn + Kp / 2;             // Kp: eigenvalue estimates
-  int* pp = reinterpret_cast<int*>(dg + Kp);
-  int* qq = pp + Kp / 2;
-  int* rank = qq + Kp / 2;             // Kp
+  float* A = smj;                      // Kp x (Kp+1): T, then the Householder vectors
+  float* V = A + (size_t)Kp * ld;      // Kp x (Kp+1): eigenvectors (columns)
+  float* td = V + (size_t)Kp * ld;     // Kp: tridiagonal diagonal (scaled)
+  float* te = td + Kp;                 // Kp: off-diagonal (scaled)
+  float* te2 = te + Kp;                // Kp: squared off-diagonal
+  float* tau = te2 + Kp;               // Kp
+  float* vb = tau + Kp;                // 2 Kp: Householder vectors of steps k and k+1
+  float* pb = vb + 2 * Kp;             // Kp: p = tau A22 v
+  float* blo = pb + Kp;                // Kp: eigenvalue brackets, then scaled eigenvalues
+  float* bhi = blo + Kp;               // Kp
+  float* dg = bhi + Kp;                // Kp: eigenvalue estimates (unscaled)
+  int* slice = reinterpret_cast<int*>(dg + Kp);  // 2 SE_THREADS: Sturm counts of the slicing pass
+  int* flg = slice + 2 * SE_THREADS;   // 2 x 2 SE_THREADS: multisection flags (double-buffered)
+  int* rank = flg + 4 * SE_THREADS;    // Kp
   int* wanted = rank + Kp;             // JB
-  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(wanted + JB) + 7) & ~uintptr_t(7));
+  int* gsz = wanted + JB;              // Kp: size of the group starting at a (0 inside a group)
+  int* glist = gsz + Kp;               // Kp: starts of the groups with two or more members
+  double* red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(glist + Kp) + 7) & ~uintptr_t(7));
   double* lamj = red + 64;             // JB
-  float* scr = reinterpret_cast<float*>(lamj + JB);  // 4 * Kp * JB refinement scratch
-  __shared__ int s_stop;
+  float* scr = reinterpret_cast<float*>(lamj + JB);  // refinement scratch: Tl, Zh, Zl
+  __shared__ float s_norm, s_gl, s_gu;
+  __shared__ int s_ng;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int half = Kp / 2;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
 
-  for (int idx = tid; idx < Kp * Kp; idx += nth) {
-    int i = idx / Kp, j = idx % Kp;
-    double v = 0.0;
-    if (i < K && j < K) v = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
-    A[i * ld + j] = (float)v;
-    V[i * ld + j] = (i == j) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  if (Kp > K && tid == 0) {  // isolated padding index, below every eigenvalue
-    float s = 0.f;
-    for (int i = 0; i < K; ++i)
-      for (int j = 0; j < K; ++j) s = fmaxf(s, fabsf(A[i * ld + j]));
-    A[K * ld + K] = -4.f * (s + 1.f) * (float)K;
+  for (int idx = tid; idx < K * K; idx += nth) {
+    const int i = idx / K, j = idx % K;
+    A[i * ld + j] = (float)(0.5 * (Tin[i * K + j] + Tin[j * K + i]));
   }
   __syncthreads();
 
-  for (int sweep = 0; sweep < 15; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int idx = tid; idx < K * K; idx += nth) {
-      int i = idx / K, j = idx % K;
-      double v = (double)A[i * ld + j];
-      tot += v * v;
-      if (i != j) off += v * v;
+  // ---- (1) tridiagonalisation
+  // Householder vector of column k below the diagonal (warp 0): v (v(0) = 1,
+  // also stored in A's column k), tau[k], te[k] = beta, td[k] = A_kk
+  auto householder = [&](int k, float* v) {
+    const int m = K - k - 1;
+    float ss = 0.f;
+    for (int i = 1 + lane; i < m; i += 32) {
+      const float x = A[(k + 1 + i) * ld + k];
+      ss = fmaf(x, x, ss);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    ss = warp_sum_f(ss);
+    const float x0 = A[(k + 1) * ld + k];
+    float t = 0.f, beta = x0, scal = 0.f;
+    if (ss > 0.f) {
+      beta = -copysignf(sqrtf(x0 * x0 + ss), x0);
+      t = (beta - x0) / beta;
+      scal = 1.f / (x0 - beta);
     }
-    if ((tid & 31) == 0) {
-      red[tid >> 5] = off;
-      red[32 + (tid >> 5)] = tot;
+    for (int i = lane; i < m; i += 32) {
+      const float vv = (i == 0) ? 1.f : A[(k + 1 + i) * ld + k] * scal;
+      v[i] = vv;
+      A[(k + 1 + i) * ld + k] = vv;
     }
-    __syncthreads();
-    if (tid == 0) {
-      double o2 = 0.0, t2 = 0.0;
-      for (int k = 0; k < (nth >> 5); ++k) {
-        o2 += red[k];
-        t2 += red[32 + k];
-      }
-      // the refinement below restores full accuracy, so the sweeps stop at
-      // off(A) <= 1e-5 ||A||_F (above the FP32 rounding floor of ~K eps ||A||)
-      s_stop = (o2 <= 1e-10 * t2) || (t2 == 0.0);
+    if (lane == 0) {
+      tau[k] = t;
+      te[k] = beta;
+      td[k] = A[k * ld + k];
     }
-    __syncthreads();
-    if (s_stop) break;
-    for (int round = 0; round < Kp - 1; ++round) {
-      if (tid < half) {
-        int p, q;
-        if (tid == 0) {
-          p = round;
-          q = Kp - 1;
-        } else {
-          p = (round + tid) % (Kp - 1);
-          q = (round - tid + (Kp - 1)) % (Kp - 1);
+  };
+  if (K >= 3 && warp == 0) householder(0, vb);
+  __syncthreads();
+  for (int k = 0; k + 2 < K; ++k) {
+    const int m = K - k - 1;
+    const float* v = vb + (k & 1) * Kp;
+    float* vn = vb + ((k + 1) & 1) * Kp;
+    const float tk = tau[k];
+    if (tk != 0.f) {  // uniform
+      {  // p = tau A22 v: four threads per row
+        const int i = tid >> 2, part = tid & 3;
+        float acc = 0.f;
+        if (i < m) {
+          const float* row = A + (size_t)(k + 1 + i) * ld + (k + 1);
+          for (int j = part; j < m; j += 4) acc = fmaf(row[j], v[j], acc);
         }
-        if (p > q) {
-          int t = p;
-          p = q;
-          q = t;
-        }
-        float apq = A[p * ld + q];
-        float app = A[p * ld + p], aqq = A[q * ld + q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-7f * sqrtf(fabsf(app * aqq)) && apq != 0.f) {
-          float tau = (aqq - app) / (2.f * apq);
-          float t;
-          if (fabsf(tau) > 1e15f) t = 0.5f / tau;
-          else t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = 1.f / sqrtf(1.f + t * t);
-          s = t * c;
-        }
-        cs[tid] = c;
-        sn[tid] = s;
-        pp[tid] = p;
-        qq[tid] = q;
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (i < m && part == 0) pb[i] = tk * acc;
       }
       __syncthreads();
-      // A <- J^T A J: every 2x2 block (pair t rows, pair u columns) transforms
-      // independently, B <- J_t^T B J_u; blocks t <= u, mirrored.
-      for (int idx = tid; idx < half * half; idx += nth) {
-        const int t = idx / half, u = idx % half;
-        if (u > t) continue;
-        const float ct = cs[t], st = sn[t], cu = cs[u], su = sn[u];
-        if (st == 0.f && su == 0.f) continue;
-        const int pt = pp[t], qt = qq[t], pu = pp[u], qu = qq[u];
-        float b00 = A[pt * ld + pu], b01 = A[pt * ld + qu], b10 = A[qt * ld + pu], b11 = A[qt * ld + qu];
-        float m00 = ct * b00 - st * b10, m01 = ct * b01 - st * b11;
-        float m10 = st * b00 + ct * b10, m11 = st * b01 + ct * b11;
-        float n00 = cu * m00 - su * m01, n01 = su * m00 + cu * m01;
-        float n10 = cu * m10 - su * m11, n11 = su * m10 + cu * m11;
-        if (t == u) {  // the rotation annihilates the pair's off-diagonal entry
-          n01 = 0.f;
-          n10 = 0.f;
+      // w = p - (tau/2)(p^T v) v, with (p^T v) reduced by every warp itself
+      float pv = 0.f;
+      for (int i = lane; i < m; i += 32) pv = fmaf(pb[i], v[i], pv);
+      const float kk = 0.5f * tk * warp_sum_f(pv);
+      if (warp == 0) {
+        // column k+1 (local column 0) first, then the next Householder vector
+        const float v0 = v[0], w0 = pb[0] - kk * v0;
+        for (int i = lane; i < m; i += 32) {
+          const float wi = pb[i] - kk * v[i];
+          float* a = &A[(k + 1 + i) * ld + (k + 1)];
+          *a = fmaf(-v[i], w0, fmaf(-wi, v0, *a));
         }
-        A[pt * ld + pu] = n00;
-        A[pt * ld + qu] = n01;
-        A[qt * ld + pu] = n10;
-        A[qt * ld + qu] = n11;
-        if (t != u) {
-          A[pu * ld + pt] = n00;
-          A[qu * ld + pt] = n01;
-          A[pu * ld + qt] = n10;
-          A[qu * ld + qt] = n11;
+        __syncwarp();
+        if (k + 3 < K) householder(k + 1, vn);
+      } else {
+        // the next trailing block (local rows and columns 1..m-1); local row 0
+        // (the upper part of row k+1) is never read again
+        const int mm = m - 1;
+        for (int idx = tid - 32; idx < mm * mm; idx += nth - 32) {
+          const int i = 1 + idx / mm, j = 1 + idx % mm;
+          const float wi = pb[i] - kk * v[i], wj = pb[j] - kk * v[j];
+          float* a = &A[(k + 1 + i) * ld + (k + 1 + j)];
+          *a = fmaf(-v[i], wj, fmaf(-wi, v[j], *a));
         }
       }
-      for (int idx = tid; idx < half * Kp; idx += nth) {  // V <- V J
-        int u = idx / Kp, i = idx % Kp;
-        float c = cs[u], s = sn[u];
-        if (s == 0.f) continue;
-        int p = pp[u], q = qq[u];
-        float vp = V[i * ld + p], vq = V[i * ld + q];
-        V[i * ld + p] = c * vp - s * vq;
-        V[i * ld + q] = s * vp + c * vq;
-      }
+      __syncthreads();
+    } else {
+      if (warp == 0 && k + 3 < K) householder(k + 1, vn);
       __syncthreads();
     }
   }
-  // eigenvalue estimates and their descending order (ties by index)
-  for (int i = tid; i < Kp; i += nth) dg[i] = A[i * ld + i];
+  if (tid == 0) {
+    if (K >= 2) {
+      td[K - 2] = A[(K - 2) * ld + (K - 2)];
+      te[K - 2] = A[(K - 1) * ld + (K - 2)];
+      tau[K - 2] = 0.f;
+    }
+    td[K - 1] = A[(K - 1) * ld + (K - 1)];
+    tau[K - 1] = 0.f;
+    float nrm = 0.f;
+    for (int i = 0; i < K; ++i) {
+      float r = fabsf(td[i]);
+      if (i > 0) r += fabsf(te[i - 1]);
+      if (i + 1 < K) r += fabsf(te[i]);
+      nrm = fmaxf(nrm, r);
+    }
+    s_norm = (nrm > 0.f) ? nrm : 1.f;
+  }
   __syncthreads();
+  // scale to unit infinity norm
+  const float tn = s_norm, itn = 1.f / s_norm;
+  for (int i = tid; i < K; i += nth) {
+    td[i] *= itn;
+    const float ei = (i + 1 < K) ? te[i] * itn : 0.f;
+    te[i] = ei;
+    te2[i] = ei * ei;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float gl = 0.f, gu = 0.f;
+    for (int i = 0; i < K; ++i) {
+      float r = 0.f;
+      if (i > 0) r += fabsf(te[i - 1]);
+      if (i + 1 < K) r += fabsf(te[i]);
+      gl = (i == 0) ? td[i] - r : fminf(gl, td[i] - r);
+      gu = (i == 0) ? td[i] + r : fmaxf(gu, td[i] + r);
+    }
+    const float pad = 4e-6f * fmaxf(fabsf(gl), fabsf(gu)) + 1e-20f;
+    s_gl = gl - pad;
+    s_gu = gu + pad;
+  }
+  __syncthreads();
+
+  // ---- (2) eigenvalues: slicing pass (two points per thread), then multisection
+  const float gl = s_gl, gu = s_gu;
+  const int P = 2 * nth;
+  {
+    const float x0 = gl + (gu - gl) * (float)(2 * tid + 1) / (float)(P + 1);
+    const float x1 = gl + (gu - gl) * (float)(2 * tid + 2) / (float)(P + 1);
+    int c0, c1;
+    sturm_count2(td, te2, K, x0, x1, c0, c1);
+    slice[2 * tid] = c0;
+    slice[2 * tid + 1] = c1;
+  }
+  __syncthreads();
+  for (int a = tid; a < K; a += nth) {  // bracket of the a-th smallest eigenvalue
+    // last slice point with count <= a (binary search; counts are non-decreasing)
+    int lo = -1, hi = P;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (slice[mid] <= a) lo = mid;
+      else hi = mid;
+    }
+    blo[a] = (lo < 0) ? gl : gl + (gu - gl) * (float)(lo + 1) / (float)(P + 1);
+    bhi[a] = (hi >= P) ? gu : gl + (gu - gl) * (float)(hi + 1) / (float)(P + 1);
+    if (bhi[a] < blo[a]) bhi[a] = blo[a];
+  }
+  __syncthreads();
+  {
+    const int G = nth / K;  // threads per eigenvalue (>= 4 for K <= 128)
+    const int NP = 2 * G;   // points per eigenvalue and step
+    const int a = tid / G, g = tid % G;
+    const bool act = a < K;
+    float lo = act ? blo[a] : 0.f, hi = act ? bhi[a] : 0.f;
+    int steps = 0;
+    for (long span = 1; span < 65536; span *= (NP + 1)) ++steps;
+    for (int st = 0; st < steps; ++st) {
+      int* f = flg + (st & 1) * 2 * SE_THREADS;
+      if (act) {
+        const float x0 = lo + (hi - lo) * (float)(2 * g + 1) / (float)(NP + 1);
+        const float x1 = lo + (hi - lo) * (float)(2 * g + 2) / (float)(NP + 1);
+        int c0, c1;
+        sturm_count2(td, te2, K, x0, x1, c0, c1);
+        f[a * NP + 2 * g] = (c0 <= a) ? 1 : 0;
+        f[a * NP + 2 * g + 1] = (c1 <= a) ? 1 : 0;
+      }
+      __syncthreads();
+      if (act) {
+        float nlo = lo, nhi = hi;
+        for (int q = 0; q < NP; ++q) {
+          const float x = lo + (hi - lo) * (float)(q + 1) / (float)(NP + 1);
+          if (f[a * NP + q]) nlo = fmaxf(nlo, x);
+          else nhi = fminf(nhi, x);
+        }
+        lo = nlo;
+        hi = fmaxf(nhi, nlo);
+      }
+    }
+    if (act && g == 0) {
+      blo[a] = 0.5f * (lo + hi);  // scaled eigenvalue
+      dg[a] = 0.5f * (lo + hi) * tn;
+    }
+  }
+  __syncthreads();
+
+  // ---- (3) eigenvectors of the tridiagonal matrix by inverse iteration
+  // Only the eigenvalues a >= a_need are wanted (all with refinement); groups
+  // of eigenvalues closer than kSeGroupTol are handled by one warp each.
+  const float* lam = blo;
+  const int a_need = refine ? 0 : max(0, K - nout);
+  if (tid == 0) {
+    int ng = 0;
+    for (int a = 0; a < K;) {
+      int last = a;
+      while (last + 1 < K && lam[last + 1] - lam[last] <= kSeGroupTol) ++last;
+      gsz[a] = last - a + 1;
+      for (int b = a + 1; b <= last; ++b) gsz[b] = 0;
+      if (last > a && last >= a_need) glist[ng++] = a;
+      a = last + 1;
+    }
+    s_ng = ng;
+  }
+  __syncthreads();
+  if (tid < K && tid >= a_need && gsz[tid] == 1) {  // isolated: one thread, three solves
+    const int b = tid;
+    TriLU f;
+    tri_lu(td, te, K, lam[b], 1.2e-7f, f);
+    float* x = V + b;  // column b, stride ld
+    for (int i = 0; i < K; ++i) x[i * ld] = hash_uniform(0x5EEDULL + (unsigned long long)b, (unsigned long long)i, 77ULL);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve(f, K, x, ld);
+      float mx = 0.f;
+      for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(x[i * ld]));
+      if (!(mx > 0.f) || !(mx < 3e38f)) {
+        for (int i = 0; i < K; ++i)
+          x[i * ld] = hash_uniform(0xBADULL + (unsigned long long)(b * 8 + it), (unsigned long long)i, 78ULL);
+        continue;
+      }
+      float ss = 0.f;
+      const float im = 1.f / mx;
+      for (int i = 0; i < K; ++i) {
+        const float v = x[i * ld] * im;
+        x[i * ld] = v;
+        ss = fmaf(v, v, ss);
+      }
+      const float is = rsqrtf(ss);
+      for (int i = 0; i < K; ++i) x[i * ld] *= is;
+    }
+  }
+  for (int gi = warp; gi < s_ng; gi += nwarps) {  // groups: lane = member, MGS in member order
+    const int a0 = glist[gi], c = gsz[a0];
+    for (int base = a0; base < a0 + c; base += 32) {
+      const int cc = min(32, a0 + c - base);
+      const int b = base + lane;
+      const bool act = lane < cc;
+      TriLU f;
+      if (act) {
+        tri_lu(td, te, K, lam[b], 1.2e-7f, f);
+        for (int i = 0; i < K; ++i)
+          V[i * ld + b] = hash_uniform(0x5EEDULL + (unsigned long long)b, (unsigned long long)i, 77ULL);
+      }
+      for (int it = 0; it < 2; ++it) {
+        if (act) tri_solve(f, K, V + b, ld);
+        __syncwarp();
+        for (int q = a0; q < base + cc; ++q) {
+          if (q >= base) warp_normalise(V, ld, K, q, lane, (unsigned long long)(q * 8 + it));
+          if (act && b > q) {
+            float d0 = 0.f, d1 = 0.f;
+            int i = 0;
+            for (; i + 1 < K; i += 2) {
+              d0 = fmaf(V[i * ld + b], V[i * ld + q], d0);
+              d1 = fmaf(V[(i + 1) * ld + b], V[(i + 1) * ld + q], d1);
+            }
+            if (i < K) d0 = fmaf(V[i * ld + b], V[i * ld + q], d0);
+            const float dot = d0 + d1;
+            for (int r = 0; r < K; ++r) V[r * ld + b] = fmaf(-dot, V[r * ld + q], V[r * ld + b]);
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- (4) back-transformation V <- H_0 ... H_{K-3} V: each warp applies all
+  // reflectors (last first) to its own columns, four at a time
+  {
+    const int ncols = K - a_need;
+    for (int c0 = warp; c0 < ncols; c0 += 4 * nwarps) {
+      int col[4];
+      bool use[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = c0 + u * nwarps;
+        use[u] = j < ncols;
+        col[u] = use[u] ? a_need + j : a_need + c0;
+      }
+      for (int k = K - 3; k >= 0; --k) {
+        const float tk = tau[k];
+        if (tk == 0.f) continue;
+        const int m = K - k - 1;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = lane; i < m; i += 32) {
+          const float vi = A[(k + 1 + i) * ld + k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = fmaf(vi, V[(k + 1 + i) * ld + col[u]], acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = tk * warp_sum_f(acc[u]);
+        for (int i = lane; i < m; i += 32) {
+          const float vi = A[(k + 1 + i) * ld + k];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (use[u]) V[(k + 1 + i) * ld + col[u]] = fmaf(-vi, acc[u], V[(k + 1 + i) * ld + col[u]]);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  if (!refine) {  // the FP32 eigenpairs as they are, in descending order
+    for (int o = tid; o < K * nout; o += nth) {
+      const int j = o / K, row = o % K;
+      Yout[(size_t)j * ldy + row] = V[row * ld + (K - 1 - j)];
+    }
+    for (int j = tid; j < nout; j += nth) theta[j] = (double)dg[K - 1 - j];
+    return;
+  }
+
+  // ---- (5) refinement of the wanted vectors: one first-order correction
+  // from accurately computed residuals.  With y_j the estimate of the j-th
+  // largest eigenvector, z = T y_j is accumulated in FP32 pairs against
+  // T = Th + Tl (T rounded to FP32 plus its rounding remainder),
+  // theta_j = y_j^T z / y_j^T y_j in FP64, r_j = z - theta_j y_j, and
+  //   y_j <- y_j + sum_{i : |theta_j - lambda_i| > delta} y_i (y_i^T r_j) / (theta_j - lambda_i)
+  // (the first-order eigenvector perturbation; once r_j is formed, FP32
+  // suffices); eigenvalues closer than delta are left to the orthonormality
+  // correction below.
   float scale = 0.f;
   for (int i = 0; i < K; ++i) scale = fmaxf(scale, fabsf(dg[i]));
-  const float delta = 1e-3f * fmaxf(scale, 1e-30f);  // eigenvalues closer than this form a cluster
-  for (int i = tid; i < K; i += nth) {
-    float di = dg[i];
-    int rk = 0;
-    for (int j = 0; j < K; ++j) {
-      float dj = dg[j];
-      rk += (dj > di) || (dj == di && j < i);
-    }
-    rank[i] = rk;
-  }
-  __syncthreads();
-  // T (symmetrised) as a packed upper triangle in the freed A region, split
-  // once into FP32 hi + lo parts (Kp (Kp+1)/2 entries each = Kp (Kp+1) floats);
-  // hi + lo carries ~48 bits, enough for the FP32-pair products below
-  float* Th = A;
-  float* Tl = A + Kp * (Kp + 1) / 2;
+  const float delta = 1e-3f * fmaxf(scale, 1e-30f);
+  float* Th = A;                             // K x K, stride ld (A is free now)
+  float* Tl = scr;                           // packed upper triangle, K (K+1) / 2
+  float* Zh = Tl + Kp * (Kp + 1) / 2;        // K x JB
+  float* Zl = Zh + Kp * JB;                  // K x JB
   for (int idx = tid; idx < K * K; idx += nth) {
-    int i = idx / K, j = idx % K;
-    if (i <= j) {
-      const double t = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
-      const float hi = (float)t;
-      Th[j * (j + 1) / 2 + i] = hi;
-      Tl[j * (j + 1) / 2 + i] = (float)(t - (double)hi);
-    }
+    const int i = idx / K, j = idx % K;
+    const double t = 0.5 * (Tin[i * K + j] + Tin[j * K + i]);
+    const float hi = (float)t;
+    Th[i * ld + j] = hi;
+    if (i <= j) Tl[j * (j + 1) / 2 + i] = (float)(t - (double)hi);
   }
   __syncthreads();
-  // refinement scratch, per pass: Ph | Pl | Sm | Rm  (each Kp x jb floats)
-  const int jb = JB;
-  float* Ph = scr;
-  float* Pl = Ph + Kp * jb;
-  float* Sm = Pl + Kp * jb;
-  float* Rm = Sm + Kp * jb;
-  for (int j0 = 0; j0 < nout; j0 += jb) {
-    const int nb = min(jb, nout - j0);
-    for (int i = tid; i < K; i += nth) {
-      int rk = rank[i];
-      if (rk >= j0 && rk < j0 + nb) wanted[rk - j0] = i;
-    }
-    __syncthreads();
-    // P = T Y_wanted  (FP32-pair accumulation, T split into hi + lo)
-    for (int o = tid; o < K * nb; o += nth) {
-      int k = o / nb, jj = o % nb;
-      const int j = wanted[jj];
+  for (int j0 = 0; j0 < nout; j0 += JB) {
+    const int nb = min(JB, nout - j0);
+    for (int o = tid; o < K * nb; o += nth) {  // z = T y_j
+      const int k = o / nb, jj = o % nb;
+      const int col = K - 1 - (j0 + jj);
       DF acc;
-      for (int l = 0; l < K; ++l) {
-        const int pi = (k <= l) ? l * (l + 1) / 2 + k : k * (k + 1) / 2 + l;
-        const float y = V[l * ld + j];
-        acc.fma_acc(Th[pi], y);
-        acc.fma_acc(Tl[pi], y);
+      float lo = 0.f;
+      const float* th = Th + k * ld;
+#pragma unroll 4
+      for (int l = 0; l < K; ++l) acc.fma_acc(th[l], V[l * ld + col]);
+      int pk = k * (k + 1) / 2;  // Tl(k, l) for l < k, then Tl(l, k) for l >= k
+      for (int l = 0; l < k; ++l) lo = fmaf(Tl[pk + l], V[l * ld + col], lo);
+      int pl = k * (k + 1) / 2 + k;
+      for (int l = k; l < K; ++l) {
+        lo = fmaf(Tl[pl], V[l * ld + col], lo);
+        pl += l + 1;
       }
-      Ph[k * jb + jj] = acc.hi;
-      Pl[k * jb + jj] = acc.lo;
+      Zh[k * JB + jj] = acc.hi;
+      Zl[k * JB + jj] = acc.lo + lo;
     }
     __syncthreads();
-    // S = Y^T P, R = I - Y^T Y_wanted
-    for (int o = tid; o < K * nb; o += nth) {
-      int i = o / nb, jj = o % nb;
-      const int j = wanted[jj];
-      DF s_acc, r_acc;
-      for (int k = 0; k < K; ++k) {
-        float yi = V[k * ld + i];
-        s_acc.fma_acc(yi, Ph[k * jb + jj]);
-        s_acc.fma_acc(yi, Pl[k * jb + jj]);
-        r_acc.fma_acc(yi, V[k * ld + j]);
+    for (int jj = warp; jj < nb; jj += nwarps) {  // theta_j: FP64 Rayleigh quotient
+      const int col = K - 1 - (j0 + jj);
+      double num = 0.0, den = 0.0;
+      for (int k = lane; k < K; k += 32) {
+        const double y = (double)V[k * ld + col];
+        num += y * ((double)Zh[k * JB + jj] + (double)Zl[k * JB + jj]);
+        den += y * y;
       }
-      double rv = (i == j ? 1.0 : 0.0) - r_acc.value();
-      if (i == j) lamj[jj] = s_acc.value() / (1.0 - rv);
-      Sm[i * jb + jj] = (float)s_acc.value();
-      Rm[i * jb + jj] = (float)rv;
+      for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+      if (lane == 0) lamj[jj] = (den > 0.0) ? num / den : 0.0;
     }
     __syncthreads();
-    // E (in place of S)
-    for (int o = tid; o < K * nb; o += nth) {
-      int i = o / nb, jj = o % nb;
-      const int j = wanted[jj];
-      float r = Rm[i * jb + jj];
-      float e;
-      float lj = (float)lamj[jj];
-      float gap = lj - dg[i];
-      if (i == j || fabsf(gap) <= delta) e = 0.5f * r;
-      else e = (Sm[i * jb + jj] + lj * r) / gap;
-      Sm[i * jb + jj] = e;
+    for (int o = tid; o < K * nb; o += nth) {  // r = z - theta y (into Zh)
+      const int k = o / nb, jj = o % nb;
+      const int col = K - 1 - (j0 + jj);
+      const double th = lamj[jj];
+      const float thh = (float)th, thl = (float)(th - (double)thh);
+      const float y = V[k * ld + col];
+      Zh[k * JB + jj] = fmaf(-thh, y, Zh[k * JB + jj]) + fmaf(-thl, y, Zl[k * JB + jj]);
     }
     __syncthreads();
-    // y_j <- y_j + Y E_j
-    for (int o = tid; o < K * nb; o += nth) {
-      int row = o / nb, jj = o % nb;
-      const int j = wanted[jj];
-      float acc = V[row * ld + j];
-      for (int i = 0; i < K; ++i) acc = fmaf(V[row * ld + i], Sm[i * jb + jj], acc);
-      Yout[(size_t)(j0 + jj) * ldy + row] = acc;
+    for (int o = tid; o < K * nb; o += nth) {  // e_ij = y_i^T r_j / (theta_j - lambda_i) (into Zl)
+      const int i = o / nb, jj = o % nb;
+      const int col = K - 1 - (j0 + jj);
+      float d0 = 0.f, d1 = 0.f;
+      int k = 0;
+#pragma unroll 2
+      for (; k + 1 < K; k += 2) {
+        d0 = fmaf(V[k * ld + i], Zh[k * JB + jj], d0);
+        d1 = fmaf(V[(k + 1) * ld + i], Zh[(k + 1) * JB + jj], d1);
+      }
+      if (k < K) d0 = fmaf(V[k * ld + i], Zh[k * JB + jj], d0);
+      const float gap = (float)lamj[jj] - dg[i];
+      Zl[i * JB + jj] = (i == col || fabsf(gap) <= delta) ? 0.f : (d0 + d1) / gap;
+    }
+    __syncthreads();
+    for (int o = tid; o < K * nb; o += nth) {  // y_j + Y e_j
+      const int row = o / nb, jj = o % nb;
+      const int col = K - 1 - (j0 + jj);
+      float a0 = V[row * ld + col], a1 = 0.f;
+      int i = 0;
+#pragma unroll 2
+      for (; i + 1 < K; i += 2) {
+        a0 = fmaf(V[row * ld + i], Zl[i * JB + jj], a0);
+        a1 = fmaf(V[row * ld + i + 1], Zl[(i + 1) * JB + jj], a1);
+      }
+      if (i < K) a0 = fmaf(V[row * ld + i], Zl[i * JB + jj], a0);
+      Yout[(size_t)(j0 + jj) * ldy + row] = a0 + a1;
     }
     for (int jj = tid; jj < nb; jj += nth) theta[j0 + jj] = lamj[jj];
     __syncthreads();
@@ -821,25 +1151,472 @@ __global__ void __launch_bounds__(512) k_jacobi(const double* __restrict__ Tin, 
   }
 }
 
-static size_t jacobi_smem(int Kp) {
-  size_t ld = Kp + 1;
-  size_t f = 2 * (size_t)Kp * ld + (size_t)Kp + (size_t)Kp;  // A, V, cs+sn, dg
-  size_t ints = (size_t)Kp + (size_t)Kp + JB;                // pp+qq, rank, wanted
-  return f * sizeof(float) + ints * sizeof(int) + 8 + (64 + JB) * sizeof(double) +
-         4 * (size_t)Kp * JB * sizeof(float);
+static size_t sym_eig_smem(int Kp) {
+  const size_t ld = Kp + 1;
+  const size_t f = 2 * (size_t)Kp * ld + 10 * (size_t)Kp;          // A, V, ten vectors
+  const size_t ints = 6 * (size_t)SE_THREADS + 3 * (size_t)Kp + JB;  // slice, flags, rank, gsz, glist, wanted
+  const size_t scr = (size_t)Kp * (Kp + 1) / 2 + 2 * (size_t)Kp * JB;  // Tl, Zh, Zl
+  return f * sizeof(float) + ints * sizeof(int) + 8 + (64 + JB) * sizeof(double) + scr * sizeof(float);
 }
 
 void init_lanczos_attributes() {
-  cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jacobi_smem(kMaxK));
+  init_orth_attributes();
+  cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_eig_smem(kMaxK));
   cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
 }
 
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
-                    const int* skip, cudaStream_t st) {
-  int Kp = (K + 1) & ~1;
-  // fewer warps for small K: the rotation rounds are barrier-bound
-  const int threads = Kp <= 32 ? 128 : (Kp <= 64 ? 256 : 512);
-  k_jacobi<<<1, threads, jacobi_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, skip);
+                    const int* skip, cudaStream_t st, int refine) {
+  const int Kp = (K + 1) & ~1;
+  k_sym_eig<<<1, SE_THREADS, sym_eig_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, refine, skip);
+}
+
+}  // namespace psdp
+
+namespace psdp {
+
+// ---------------------------------------------------------------------------
+// Block orthogonalisation in one thread-block cluster
+// ---------------------------------------------------------------------------
+// Z (n x W, column stride ldq, read from `src`) is orthogonalised against the
+// orthonormal basis Q[:, :c0] and within itself by `passes` rounds of
+//   H = Q^T Z,  Z <- Z - Q H,  G = Z^T Z,  then either
+//   (Cholesky-QR)   D = diag(G), D^{-1/2} G D^{-1/2} = R^T R, Z <- Z D^{-1/2} R^{-1}
+//   (Newton-Schulz) Z <- Z (3I - G) / 2, which maps G = I + E to I + O(E^2),
+// and written to Q[:, c0:c0+W].  The first pass of a call with chol_first
+// uses Cholesky-QR; every other pass uses the Newton-Schulz step when
+// max |G - I| <= 0.1 and Cholesky-QR otherwise.  The C CTAs of one cluster
+// each keep a slice of rows of Z and of Q[:, :c0] in shared memory for the
+// whole call.  H and G are per-CTA partial sums, combined through
+// distributed shared memory: CTA c adds slice c of the entries over the C
+// partials in CTA order (deterministic), then every CTA gathers the full
+// matrix, so every CTA takes the same decisions.  The Cholesky factor of the
+// unit-diagonal Gram matrix is computed in FP32 by one warp (Crout order:
+// row j of R from the rows above it); a pivot below kOrthDefTol marks its
+// column as dependent, and that column is replaced by pseudo-random entries
+// which the next pass orthogonalises.
+constexpr float kOrthDefTol = 1e-5f;
+constexpr float kOrthNsTol = 0.1f;
+
+struct OrthLayout {
+  int rows, ldz, ldqs, c0;
+  size_t zs, qs, tmp, ph, pg, hf, gd, rf, total;  // byte offsets
+};
+
+__host__ __device__ inline OrthLayout orth_layout(int rows, int c0, int W) {
+  OrthLayout L;
+  L.rows = rows;
+  L.c0 = c0;
+  L.ldz = W + 4;
+  L.ldqs = ((rows + 3) / 4) * 4 + 4;
+  const int rows4 = ((rows + 3) / 4) * 4;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += (bytes + 15) & ~size_t(15);
+    return at;
+  };
+  L.zs = take((size_t)rows4 * L.ldz * 4);
+  L.qs = take((size_t)(c0 > 0 ? c0 : 1) * L.ldqs * 4);
+  L.tmp = take(8192 * 4);  // split-row partial tiles: <= max(c0*W, 3*48*48, 7*32*32, 25*16*16) floats
+  L.ph = take((size_t)(c0 > 0 ? c0 : 1) * W * 4);
+  L.pg = take((size_t)W * W * 8);
+  L.hf = take((size_t)(c0 > 0 ? c0 : 1) * W * 4);
+  L.gd = take((size_t)W * W * 4);
+  L.rf = take((size_t)W * W * 4);
+  L.total = o;
+  return L;
+}
+
+// Sum over the C CTAs of a cluster of entry o of `part` (in CTA order); the
+// C remote loads are issued before the additions.
+template <typename T>
+__device__ __forceinline__ T cluster_sum(cooperative_groups::cluster_group& cl, T* part, int C, int o) {
+  T v[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) v[c] = (c < C) ? cl.map_shared_rank(part, c)[o] : T(0);
+  T s = T(0);
+#pragma unroll
+  for (int c = 0; c < 16; ++c) s += v[c];
+  return s;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, int ldq, const float* src, int n,
+                                                      int c0, int rows, int passes, int chol_first,
+                                                      unsigned long long seed, const int* skip) {
+  namespace cg = cooperative_groups;
+  if (skip && *(volatile const int*)skip) return;  // uniform over the grid
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const OrthLayout L = orth_layout(rows, c0, W);
+  extern __shared__ __align__(16) unsigned char osm[];
+  float* Zs = reinterpret_cast<float*>(osm + L.zs);
+  float* Qs = reinterpret_cast<float*>(osm + L.qs);
+  float* Tmp = reinterpret_cast<float*>(osm + L.tmp);
+  float* PartH = reinterpret_cast<float*>(osm + L.ph);
+  double* PartG = reinterpret_cast<double*>(osm + L.pg);
+  float* Hf = reinterpret_cast<float*>(osm + L.hf);
+  float* Gh = reinterpret_cast<float*>(osm + L.gd);  // scaled Gram (upper), then R
+  float* X = reinterpret_cast<float*>(osm + L.rf);   // Newton-Schulz factor
+  __shared__ float sc[W], rd[W];
+  __shared__ double d0s[W];
+  __shared__ int fl[W];
+  __shared__ unsigned s_dev;  // max |G - I| as float bits (non-negative)
+  const int tid = threadIdx.x;
+  const int ldz = L.ldz, ldqs = L.ldqs;
+  const int i0 = rank * rows;
+  const int nr = max(0, min(rows, n - i0));
+  const int rows4 = ((rows + 3) / 4) * 4;
+  // stage my rows of Z (row-major) and of Q[:, :c0] (column-major); padding rows are zero
+  for (int idx = tid; idx < rows4 * W; idx += 256) {
+    const int b = idx / rows4, i = idx % rows4;
+    Zs[i * ldz + b] = (i < nr) ? __ldg(&src[(size_t)b * ldq + i0 + i]) : 0.f;
+  }
+  for (int idx = tid; idx < rows4 * c0; idx += 256) {
+    const int a = idx / rows4, i = idx % rows4;
+    Qs[a * ldqs + i] = (i < nr) ? __ldg(&Q[(size_t)a * ldq + i0 + i]) : 0.f;
+  }
+  __syncthreads();
+  constexpr int nTb = W / 4;
+  for (int pass = 0; pass < passes; ++pass) {
+    // without the H phase, no cluster barrier separates the previous pass's
+    // gather of PartG from this pass's partial writes
+    if (c0 == 0 && pass > 0) cluster.sync();
+    if (c0 > 0) {
+      // ---- partial H = Qs^T Zs: 4x4 register tiles, rows split over idle threads
+      const int nT = (c0 / 4) * nTb;
+      const int rs = max(1, 256 / nT);
+      const int rlen = (rows4 + rs - 1) / rs;
+      const int cw = c0 * W;
+      if (tid < nT * rs) {
+        const int t = tid % nT, p = tid / nT;
+        const int ta = t / nTb, tb = t % nTb;
+        float acc[4][4] = {};
+        const int ib = p * rlen, ie = min(rows4, ib + rlen);
+        for (int i = ib; i < ie; ++i) {
+          const float4 z = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float q = Qs[(4 * ta + k) * ldqs + i];
+            acc[k][0] = fmaf(q, z.x, acc[k][0]);
+            acc[k][1] = fmaf(q, z.y, acc[k][1]);
+            acc[k][2] = fmaf(q, z.z, acc[k][2]);
+            acc[k][3] = fmaf(q, z.w, acc[k][3]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          *reinterpret_cast<float4*>(&Tmp[p * cw + (4 * ta + k) * W + 4 * tb]) =
+              make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+      }
+      __syncthreads();
+      for (int o = tid; o < cw; o += 256) {
+        float s = 0.f;
+        for (int p = 0; p < rs; ++p) s += Tmp[p * cw + o];
+        PartH[o] = s;
+      }
+      cluster.sync();
+      // reduce-scatter (slice `rank` of the entries, summed in CTA order), then all-gather
+      const int chunk = (cw + C - 1) / C;
+      for (int o = rank * chunk + tid; o < min(cw, (rank + 1) * chunk); o += 256)
+        PartH[o] = cluster_sum(cluster, PartH, C, o);  // only this CTA touches slice `rank` now
+      cluster.sync();
+      for (int o0 = tid; o0 < cw; o0 += 4 * 256) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int o = o0 + 256 * u;
+          v[u] = (o < cw) ? cluster.map_shared_rank(PartH, o / chunk)[o] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (o0 + 256 * u < cw) Hf[o0 + 256 * u] = v[u];
+      }
+      __syncthreads();
+      // ---- Zs <- Zs - Qs Hf on my rows (4x4 tiles)
+      const int nU = (rows4 / 4) * nTb;
+      for (int t = tid; t < nU; t += 256) {
+        const int ti = t / nTb, tb = t % nTb;
+        float acc[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 z = *reinterpret_cast<const float4*>(&Zs[(4 * ti + k) * ldz + 4 * tb]);
+          acc[k][0] = z.x;
+          acc[k][1] = z.y;
+          acc[k][2] = z.z;
+          acc[k][3] = z.w;
+        }
+        for (int a = 0; a < c0; ++a) {
+          const float4 q = *reinterpret_cast<const float4*>(&Qs[a * ldqs + 4 * ti]);
+          const float4 h = *reinterpret_cast<const float4*>(&Hf[a * W + 4 * tb]);
+          const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            acc[k][0] = fmaf(-qv[k], h.x, acc[k][0]);
+            acc[k][1] = fmaf(-qv[k], h.y, acc[k][1]);
+            acc[k][2] = fmaf(-qv[k], h.z, acc[k][2]);
+            acc[k][3] = fmaf(-qv[k], h.w, acc[k][3]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          *reinterpret_cast<float4*>(&Zs[(4 * ti + k) * ldz + 4 * tb]) =
+              make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+      }
+      __syncthreads();
+    }
+    // ---- partial G = Zs^T Zs on the upper 4x4 tiles
+    {
+      const int nT = nTb * (nTb + 1) / 2;
+      const int rs = max(1, 256 / nT);
+      const int rlen = (rows4 + rs - 1) / rs;
+      const int ww = W * W;
+      if (tid < nT * rs) {
+        int t = tid % nT;
+        const int p = tid / nT;
+        int ta = 0;
+        while (t >= nTb - ta) {
+          t -= nTb - ta;
+          ++ta;
+        }
+        const int tb = ta + t;
+        float acc[4][4] = {};
+        const int ib = p * rlen, ie = min(rows4, ib + rlen);
+        for (int i = ib; i < ie; ++i) {
+          const float4 za = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * ta]);
+          const float4 zb = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
+          const float av[4] = {za.x, za.y, za.z, za.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            acc[k][0] = fmaf(av[k], zb.x, acc[k][0]);
+            acc[k][1] = fmaf(av[k], zb.y, acc[k][1]);
+            acc[k][2] = fmaf(av[k], zb.z, acc[k][2]);
+            acc[k][3] = fmaf(av[k], zb.w, acc[k][3]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          *reinterpret_cast<float4*>(&Tmp[p * ww + (4 * ta + k) * W + 4 * tb]) =
+              make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+      }
+      __syncthreads();
+      for (int o = tid; o < ww; o += 256) {
+        const int a = o / W, b = o % W;
+        double s = 0.0;
+        if (a / 4 <= b / 4)
+          for (int p = 0; p < rs; ++p) s += (double)Tmp[p * ww + o];
+        PartG[o] = s;
+      }
+      if (tid == 0) s_dev = 0u;
+      cluster.sync();
+      const int chunk = (ww + C - 1) / C;
+      for (int o = rank * chunk + tid; o < min(ww, (rank + 1) * chunk); o += 256)
+        PartG[o] = cluster_sum(cluster, PartG, C, o);
+      cluster.sync();
+      // gather the diagonal first (for the scaling), then the upper triangle:
+      // scaled into Gh, and max |G - I| for the choice of the orthonormalisation
+      for (int j = tid; j < W; j += 256) {
+        const int o = j * W + j;
+        const double d = cluster.map_shared_rank(PartG, o / chunk)[o];
+        d0s[j] = d;
+        sc[j] = (d > 0.0) ? (float)(1.0 / sqrt(d)) : 0.f;
+      }
+      __syncthreads();
+      float dev = 0.f;
+      for (int o0 = tid; o0 < ww; o0 += 4 * 256) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int o = o0 + 256 * u;
+          v[u] = (o < ww && (o / W) <= (o % W)) ? cluster.map_shared_rank(PartG, o / chunk)[o] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int o = o0 + 256 * u;
+          if (o < ww) {
+            const int a = o / W, b = o % W;
+            Gh[o] = (a <= b) ? (float)(v[u] * (double)sc[a] * (double)sc[b]) : 0.f;
+            if (a <= b) dev = fmaxf(dev, (float)fabs(v[u] - (a == b ? 1.0 : 0.0)));
+          }
+        }
+      }
+      if (!(dev == dev)) dev = 3e38f;
+      atomicMax(&s_dev, __float_as_uint(dev));
+      __syncthreads();
+    }
+    const bool newton = !(pass == 0 && chol_first) && (__uint_as_float(s_dev) <= kOrthNsTol);  // CTA-uniform
+    const unsigned long long pseed = seed * 131ULL + (unsigned long long)(pass * 7 + c0);
+    if (newton) {
+      // ---- Z <- Z (3I - G)/2, one row per thread; G from the unscaled upper triangle
+      for (int o = tid; o < W * W; o += 256) {
+        const int a = o / W, b = o % W;
+        const int lo = min(a, b), hi = max(a, b);
+        const float g = (sc[lo] > 0.f && sc[hi] > 0.f) ? Gh[lo * W + hi] / (sc[lo] * sc[hi]) : 0.f;
+        X[o] = (a == b ? 1.5f : 0.f) - 0.5f * g;
+      }
+      __syncthreads();
+      for (int i = tid; i < nr; i += 256) {
+        float y[W];
+#pragma unroll
+        for (int l = 0; l < W; ++l) y[l] = 0.f;
+        for (int k = 0; k < W; ++k) {
+          const float zk = Zs[i * ldz + k];
+#pragma unroll
+          for (int m = 0; m < W / 4; ++m) {
+            const float4 x = *reinterpret_cast<const float4*>(&X[k * W + 4 * m]);
+            y[4 * m + 0] = fmaf(zk, x.x, y[4 * m + 0]);
+            y[4 * m + 1] = fmaf(zk, x.y, y[4 * m + 1]);
+            y[4 * m + 2] = fmaf(zk, x.z, y[4 * m + 2]);
+            y[4 * m + 3] = fmaf(zk, x.w, y[4 * m + 3]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < W / 4; ++m)
+          *reinterpret_cast<float4*>(&Zs[i * ldz + 4 * m]) = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+      }
+    } else {
+      // ---- Cholesky of the unit-diagonal Gram matrix by warp 0 (Crout order,
+      // R in place of Gh's upper triangle, row j from rows 0..j-1)
+      if (tid < 32) {
+        const int lane = tid;
+        for (int j = 0; j < W; ++j) {
+          float sv[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int l = j + lane + 32 * h;
+            float s0 = 0.f, s1 = 0.f;
+            if (l < W) {
+              s0 = Gh[j * W + l];
+              int i = 0;
+              for (; i + 1 < j; i += 2) {
+                s0 = fmaf(-Gh[i * W + j], Gh[i * W + l], s0);
+                s1 = fmaf(-Gh[(i + 1) * W + j], Gh[(i + 1) * W + l], s1);
+              }
+              if (i < j) s0 = fmaf(-Gh[i * W + j], Gh[i * W + l], s0);
+            }
+            sv[h] = s0 + s1;
+          }
+          const float piv = __shfl_sync(0xffffffffu, sv[0], 0);
+          const bool def = !(piv > kOrthDefTol);
+          const float inv = def ? 0.f : rsqrtf(piv);
+          __syncwarp();  // every lane has read the entries of row j it needs
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int l = j + lane + 32 * h;
+            if (l < W) Gh[j * W + l] = (l == j) ? (def ? 1.f : piv * inv) : sv[h] * inv;
+          }
+          if (lane == 0) {
+            rd[j] = def ? 1.f : inv;
+            fl[j] = (def || d0s[j] <= 0.0) ? 1 : 0;
+          }
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // ---- Z <- Z D^{-1/2} R^{-1} by forward substitution, one row per thread
+      // (x_j = (z_j - sum_{k<j} x_k R_kj) / R_jj; dependent columns get pseudo-random entries)
+      for (int i = tid; i < nr; i += 256) {
+        float* zr = Zs + i * ldz;
+        for (int j = 0; j < W; ++j) {
+          float s0 = zr[j] * sc[j], s1 = 0.f;
+          int k = 0;
+          for (; k + 1 < j; k += 2) {
+            s0 = fmaf(-zr[k], Gh[k * W + j], s0);
+            s1 = fmaf(-zr[k + 1], Gh[(k + 1) * W + j], s1);
+          }
+          if (k < j) s0 = fmaf(-zr[k], Gh[k * W + j], s0);
+          float x = (s0 + s1) * rd[j];
+          if (fl[j]) x = hash_uniform(pseed, (unsigned long long)(i0 + i), (unsigned long long)(1000 + j));
+          zr[j] = x;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nr * W; idx += 256) {
+    const int b = idx / nr, i = idx % nr;
+    Q[(size_t)(c0 + b) * ldq + i0 + i] = Zs[i * ldz + b];
+  }
+  cluster.sync();  // no CTA exits while another may still read its shared memory
+}
+
+constexpr size_t kOrthSmemMax = 200 * 1024;
+static int g_orth_cluster_max = 8;  // largest cluster size the device can co-schedule
+
+template <int W>
+static void orth_attr() {
+  cudaFuncSetAttribute(k_orth_cluster<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOrthSmemMax);
+  cudaFuncSetAttribute(k_orth_cluster<W>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+void init_orth_attributes() {
+  orth_attr<16>();
+  orth_attr<32>();
+  orth_attr<48>();
+  orth_attr<64>();
+  // can a 16-CTA cluster with the largest footprint be scheduled?
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = kOrthSmemMax;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, k_orth_cluster<64>, &cfg) == cudaSuccess && nclusters > 0)
+    g_orth_cluster_max = 16;
+  else
+    g_orth_cluster_max = 8;
+  cudaGetLastError();
+}
+
+// Cluster size and rows per CTA for the fused kernel, or 0 if it does not apply.
+static int orth_plan(int n, int c0, int w, int* csize) {
+  if (w % 16 != 0 || w > kMaxW || c0 % 16 != 0 || c0 + w > kMaxK) return 0;
+  for (int C = 8; C <= g_orth_cluster_max; C *= 2) {
+    const int rows = (n + C - 1) / C;
+    if (C < g_orth_cluster_max && rows > 128) continue;  // prefer more CTAs for long blocks
+    if (orth_layout(rows, c0, w).total <= kOrthSmemMax) {
+      *csize = C;
+      return rows;
+    }
+  }
+  return 0;
+}
+
+bool orth_cluster_applies(int n, int c0, int w) {
+  int C = 0;
+  return orth_plan(n, c0, w, &C) > 0;
+}
+
+void launch_orth_cluster(float* Q, int ldq, const float* src, int n, int c0, int w, int passes,
+                         int chol_first, unsigned long long seed, const int* skip, cudaStream_t st) {
+  int C = 0;
+  const int rows = orth_plan(n, c0, w, &C);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = orth_layout(rows, c0, w).total;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  switch (w) {
+    case 16: cudaLaunchKernelEx(&cfg, k_orth_cluster<16>, Q, ldq, src, n, c0, rows, passes, chol_first, seed, skip); break;
+    case 32: cudaLaunchKernelEx(&cfg, k_orth_cluster<32>, Q, ldq, src, n, c0, rows, passes, chol_first, seed, skip); break;
+    case 48: cudaLaunchKernelEx(&cfg, k_orth_cluster<48>, Q, ldq, src, n, c0, rows, passes, chol_first, seed, skip); break;
+    default: cudaLaunchKernelEx(&cfg, k_orth_cluster<64>, Q, ldq, src, n, c0, rows, passes, chol_first, seed, skip); break;
+  }
 }
 
 }  // namespace psdp

@@ -82,7 +82,7 @@ __device__ void reduce_partials(const double* part, int P, int stride, int L, do
 // ---------------------------------------------------------------------------
 constexpr int RZ_RB = 32;
 
-__global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, int r, int s_steps,
+__global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, int r, int s_steps, int cycle_launches,
                                               cudaGraphConditionalHandle cond, int use_cond) {
   Ctl* ctl = wk.ctl;
   if (*(volatile int*)&ctl->lz_done) return;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     ctl->lz_cycle += 1;
     ctl->lz_cycles_total += 1;
     ctl->matvecs += s_steps;
-    ctl->launches += 12LL * s_steps + 3;  // copy + 10 orthogonalisation kernels + product per step; Gram, Jacobi, Ritz
+    ctl->launches += cycle_launches;  // kernels of one restart cycle, counted by the host at enqueue time
     bool ok = worst <= ctl->lz_tol || !(worst == worst);
     if (ok || ctl->lz_cycle >= ctl->max_cycles) {
       if (!ok) ctl->lz_unconverged += 1;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_dvals(DevProblem pb, DevWork wk) {
 // G is the Gram of the column-major factor slots [slot0 | slot1] (2*kMaxR
 // columns); X = V_s Lambda_+ V_s^T for slot s, so
 // ||X1 - X0||_F^2 = sum lam1 lam1 G11^2 + sum lam0 lam0 G00^2 - 2 sum lam1 lam0 G10^2.
-__device__ void control_tail(const DevProblem& pb, const DevWork& wk, const double* G,
+__device__ void control_tail(const DevProblem& pb, const DevWork& wk, const double* G, int iter_launches,
                              cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sh[32 * 3];
   Ctl* ctl = wk.ctl;
@@ -406,7 +406,7 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
   ctl->lam_r = lam_r;
   ctl->normX = normX;
   ctl->matvecs += 1;  // warm-start product of the next iteration
-  ctl->launches += ctl->full_eig_path ? 7 : 8;  // per-iteration kernels outside the restart cycles
+  ctl->launches += iter_launches;  // per-iteration kernels outside the restart cycles (host count)
   const double comb = eps_p + eps_d;
   const int win = ctl->window;
   const double old = ctl->hist[it % win];
@@ -469,7 +469,8 @@ struct DFc {
 };
 
 __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk, int act, int rows_per_split,
-                                                      cudaGraphConditionalHandle cond, int use_cond) {
+                                                      int iter_launches, cudaGraphConditionalHandle cond,
+                                                      int use_cond) {
   namespace cg = cooperative_groups;
   __shared__ float As[GC_RC][GC_T + 1];
   __shared__ float Bs[GC_RC][GC_T + 1];
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk,
   if (!s_last) return;
   __threadfence();
   if (tid == 0) cnt[0] = 0u;
-  control_tail(pb, wk, wk.Hx, cond, use_cond);
+  control_tail(pb, wk, wk.Hx, iter_launches, cond, use_cond);
 }
 
 // ---------------------------------------------------------------------------
@@ -613,7 +614,7 @@ __global__ void k_copy_cols(const float* src, int lds_, float* dst, int ldd, int
   dst[(size_t)c * ldd + i] = src[(size_t)c * lds_ + i];
 }
 
-// Full projection (n <= 128): eigenvectors of S from the dense Jacobi solve
+// Full projection (n <= 128): eigenvectors of S from the dense one-block eigensolver
 // become the factors of the new iterate (all n of them).
 __global__ void k_full_eig_factors(DevWork wk, int n) {
   Ctl* ctl = wk.ctl;
@@ -689,10 +690,10 @@ void init_pdhg_attributes() {
   cudaFuncSetAttribute(k_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rebuild_smem(kMaxR));
 }
 
-void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
+void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps, int cycle_launches,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
   int blocks = (n + RZ_RB - 1) / RZ_RB;
-  k_ritz<<<blocks, 256, ritz_smem(K, w), st>>>(wk, n, K, w, r, s_steps, cond, use_cond);
+  k_ritz<<<blocks, 256, ritz_smem(K, w), st>>>(wk, n, K, w, r, s_steps, cycle_launches, cond, use_cond);
 }
 
 void launch_mxdual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
@@ -707,7 +708,7 @@ void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st) {
   k_dvals<<<blocks, 256, 0, st>>>(pb, wk);
 }
 
-void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
+void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int iter_launches,
                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st) {
   const int per = (act + GC_T - 1) / GC_T;
   const int tiles = per * 2 * per * 2;
@@ -725,7 +726,7 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_gram_control, pb, wk, act, rows, cond, use_cond);
+  cudaLaunchKernelEx(&cfg, k_gram_control, pb, wk, act, rows, iter_launches, cond, use_cond);
 }
 
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st) {

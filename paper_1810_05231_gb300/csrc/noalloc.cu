@@ -19,10 +19,6 @@
 
 namespace psdp {
 
-void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed, const int* skip,
-                  cudaStream_t st);
-void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r, unsigned long long seed,
-                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 void set_global_error(const std::string& msg);
 
 namespace {

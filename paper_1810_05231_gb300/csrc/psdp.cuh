@@ -13,9 +13,9 @@
 namespace psdp {
 
 constexpr int kMaxWindow = 1024;  // longest stall window l (Sec. 3.2)
-constexpr int kMaxK = 128;        // largest Rayleigh-Ritz basis (one-CTA Jacobi)
+constexpr int kMaxK = 128;        // largest Rayleigh-Ritz basis (one-block eigensolver)
 constexpr int kMaxW = 64;         // largest Lanczos block width
-constexpr int kFullEigMax = 128;  // n up to which the projection uses dense Jacobi
+constexpr int kFullEigMax = 128;  // n up to which the projection uses the dense eigensolver
 constexpr int kTile = 64;         // rebuild tile edge
 constexpr int kRedSlots = 16;     // scalar reductions per kernel
 constexpr int kMaxR = 128;        // largest factor rank held (full projection up to n = 128)
@@ -51,7 +51,7 @@ struct Ctl {
   int max_rank;
   int max_cycles;
   int fixed_rank;    // 1: never change r (building-block use)
-  int full_eig_path; // projection by dense Jacobi (n <= 128 or Alg. 1)
+  int full_eig_path; // projection by the dense eigensolver (n <= 128 or Alg. 1)
   int pad1;
   long long matvecs;
   long long lz_cycles_total;
@@ -160,20 +160,29 @@ void launch_chol_inv(const double* G, int w, float* Rinv, int* flags, const int*
 // Z <- Z * R^{-1}; deficient columns replaced by pseudo-random vectors.
 void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* flags, int n,
                        unsigned long long seed, const int* skip, cudaStream_t st);
+// Eigenpairs of the symmetric K x K T (FP64 row-major, K <= 128): the nout
+// algebraically largest, descending, to theta / Y (columns, stride ldy).
+// refine = 1 (default) corrects the wanted vectors once from residuals
+// accumulated in FP32 pairs and returns FP64 Rayleigh quotients; refine = 0
+// returns the FP32 eigenpairs of the tridiagonal method as they are.
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
-                    const int* skip, cudaStream_t st);
+                    const int* skip, cudaStream_t st, int refine = 1);
 void init_lanczos_attributes();
+void init_orth_attributes();
+bool orth_cluster_applies(int n, int c0, int w);
+void launch_orth_cluster(float* Q, int ldq, const float* src, int n, int c0, int w, int passes,
+                         int chol_first, unsigned long long seed, const int* skip, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // launchers (k_pdhg.cu)
 // ---------------------------------------------------------------------------
-void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps,
+void launch_ritz(const DevWork& wk, int n, int K, int w, int r, int s_steps, int cycle_launches,
                  cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 // M(X^{k+1}) from the factors fused with the dual step and its reductions.
 void launch_mxdual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
 void launch_dvals(const DevProblem& pb, const DevWork& wk, cudaStream_t st);
 // Gram of the factor slots (columns < act of each slot) fused with the controller.
-void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act,
+void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int iter_launches,
                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 // sel = 0: factors of the current iterate (Ctl::par); sel = 1: the other buffer.
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st);

@@ -20,6 +20,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <mutex>
+
 #include "solver.h"
 
 namespace psdp {
@@ -72,12 +74,18 @@ static void dbg(const DevWork& wk, const char* tag, cudaStream_t st) {
   }
 }
 
+// Function attributes are per device: set them once on each device, under a
+// lock (solves of a batch start from several host threads).
 void init_kernel_attributes() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex mu;
+  static bool done[256] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 256 || done[dev]) return;
   init_pdhg_attributes();
   init_lanczos_attributes();
-  done = true;
+  done[dev] = true;
 }
 
 Solver::~Solver() { free_all(); }
@@ -246,8 +254,14 @@ int Solver::set_ctl_fields(int status, int it_stop, int rr, int w, int K, int k_
 // two passes of (classical Gram-Schmidt, Cholesky QR); columns found
 // dependent in the first pass are refilled with pseudo-random vectors.
 void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed,
-                  const int* skip, cudaStream_t st) {
+                  const int* skip, cudaStream_t st, const float* src) {
   float* Z = wk.Q + (size_t)c0 * wk.ldq;
+  if (orth_cluster_applies(n, c0, w)) {  // the whole orthogonalisation in one cluster launch
+    launch_orth_cluster(wk.Q, wk.ldq, src ? src : Z, n, c0, w, 2, 1, seed, skip, st);
+    dbg(wk, "orth cluster", st);
+    return;
+  }
+  if (src) launch_copy_cols(src, wk.ldq, Z, wk.ldq, n, w, skip, st);
   unsigned* cnt = wk.counters + CNT_GRAM * 512;
   for (int pass = 0; pass < 2; ++pass) {
     if (c0 > 0) {
@@ -269,6 +283,10 @@ void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long se
 // One Cholesky-QR pass on Q[:, c0:c0+w] (re-orthonormalises the kept Ritz block).
 static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned long long seed, cudaStream_t st) {
   float* Z = wk.Q + (size_t)c0 * wk.ldq;
+  if (orth_cluster_applies(n, c0, w)) {
+    launch_orth_cluster(wk.Q, wk.ldq, Z, n, c0, w, 1, 0, seed, nullptr, st);
+    return;
+  }
   unsigned* cnt = wk.counters + CNT_GRAM * 512;
   launch_gram(Z, wk.ldq, w, Z, wk.ldq, w, n, wk.H, wk.part, cnt, nullptr, st);
   launch_chol_inv(wk.H, w, wk.Hf, wk.flags, nullptr, st);
@@ -280,9 +298,7 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
                    cudaStream_t st) {
   const int* skip = &wk.ctl->lz_done;
   for (int j = 1; j <= s; ++j) {
-    launch_copy_cols(wk.W + (size_t)(j - 1) * w * wk.ldq, wk.ldq, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
-                     n, w, skip, st);
-    enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st);
+    enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st, wk.W + (size_t)(j - 1) * w * wk.ldq);
     launch_block_matvec(wk.S, wk.lds, n, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
                         wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st, wk.mv_part, wk.mv_cnt);
     dbg(wk, "cycle matvec", st);
@@ -290,8 +306,10 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
   launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
   dbg(wk, "rr gram T", st);
   launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st);
-  dbg(wk, "rr jacobi", st);
-  launch_ritz(wk, n, K, w, r, s, cond, use_cond, st);
+  dbg(wk, "rr eig", st);
+  int cycle_launches = 3 + s;  // Gram of T, eigensolver, Ritz; one product per step
+  for (int j = 1; j <= s; ++j) cycle_launches += orth_cluster_applies(n, j * w, w) ? 1 : 11;
+  launch_ritz(wk, n, K, w, r, s, cycle_launches, cond, use_cond, st);
   dbg(wk, "ritz", st);
 }
 
@@ -305,7 +323,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
     launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, st);
     launch_full_eig_factors(wk, n, st);
   } else {
-    g_debug_n = n;
+    if (g_debug) g_debug_n = n;
     enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
     launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, wk.mv_part, wk.mv_cnt,
                         inner, use);
@@ -347,7 +365,9 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   launch_dvals(pb, wk, st);
   dbg(wk, "mxdual/dvals", st);
   const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
-  launch_gram_control(pb, wk, act, outer, use, st);
+  // kernels per iteration outside the restart cycles
+  const int iter_launches = k.full ? 7 : (orth_cluster_applies(n, 0, k.w) ? 1 : 3) + 5;
+  launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
   dbg(wk, "gram+control", st);
   launch_rebuild(pb, wk, k.r, 0, st);
   dbg(wk, "rebuild", st);
@@ -649,7 +669,7 @@ int Solver::set_iterate(int rr, const double* V, const double* lam, const double
   return PROXSDP_OK;
 }
 
-// aproj(S, r) on caller memory: Lanczos (or dense Jacobi for n <= 128) on S,
+// aproj(S, r) on caller memory: Lanczos (or the dense eigensolver for n <= 128) on S,
 // then P = V diag(max(lambda,0)) V^T through the rebuild kernel.
 int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float* V, double* lambda,
                  const proxsdp_gpu_settings& set, cudaStream_t st_in, proxsdp_gpu_info* info,
@@ -768,7 +788,7 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
 }
 
 int sym_eig_device(const double* T, int K, double* theta, float* Y, cudaStream_t st) {
-  launch_sym_eig(T, K, theta, Y, K, K, nullptr, st);
+  launch_sym_eig(T, K, theta, Y, K, K, nullptr, st, 1);
   return cudaGetLastError() == cudaSuccess ? PROXSDP_OK : PROXSDP_ERR_CUDA;
 }
 

@@ -84,5 +84,11 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
                  std::string& err);
 int sym_eig_device(const double* T, int K, double* theta, float* Y, cudaStream_t st);
 void init_kernel_attributes();
+// Orthonormalise Q[:, c0:c0+w] (read from `src` when given) against Q[:, :c0]
+// and within itself; one restart cycle of the block Krylov projection.
+void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed, const int* skip,
+                  cudaStream_t st, const float* src = nullptr);
+void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r, unsigned long long seed,
+                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 
 }  // namespace psdp
