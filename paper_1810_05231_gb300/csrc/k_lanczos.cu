@@ -565,6 +565,7 @@ constexpr int JB = 32;  // wanted columns refined per pass
 constexpr int SE_THREADS = 512;
 constexpr float kSePivmin = 1e-30f;   // Sturm pivots below this (unit-norm matrix) count as negative
 constexpr float kSeGroupTol = 1e-3f;  // inverse-iteration groups (unit-norm matrix)
+constexpr double kRefineBelow = 2e-5;  // adaptive refinement: Ritz residual tolerances below this
 
 // Numbers of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal)
 // below x0 and below x1 (two interleaved Sturm sequences).
@@ -625,18 +626,21 @@ __device__ void tri_lu(const float* d, const float* e, int K, float lam, float t
 
 // x <- (T - lam I)^{-1} x for the factorisation above; x has stride ld.
 __device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
+  float a = x[0];  // the current row's entry, carried in a register
+#pragma unroll 4
   for (int i = 0; i < K - 1; ++i) {
-    float a = x[i * ld], b = x[(i + 1) * ld];
+    float b = x[(i + 1) * ld];
     if ((f.sw[i >> 5] >> (i & 31)) & 1u) {
       const float t = a;
       a = b;
       b = t;
-      x[i * ld] = a;
     }
-    x[(i + 1) * ld] = b - f.l[i] * a;
+    x[i * ld] = a;
+    a = fmaf(-f.l[i], a, b);
   }
-  float x2 = 0.f, x1 = x[(K - 1) * ld] * f.u0[K - 1];
+  float x2 = 0.f, x1 = a * f.u0[K - 1];
   x[(K - 1) * ld] = x1;
+#pragma unroll 4
   for (int i = K - 2; i >= 0; --i) {
     const float xi = (x[i * ld] - f.u1[i] * x1 - f.u2[i] * x2) * f.u0[i];
     x[i * ld] = xi;
@@ -679,8 +683,12 @@ __device__ void warp_normalise(float* V, int ld, int K, int q, int lane, unsigne
 
 __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict__ Tin, int K, int Kp,
                                                         double* __restrict__ theta, float* __restrict__ Yout,
-                                                        int ldy, int nout, int refine, const int* skip) {
+                                                        int ldy, int nout, int refine, const double* adapt_tol,
+                                                        const int* skip) {
   if (skip && *(volatile const int*)skip) return;
+  // adaptive mode: refine only when the projection's tolerance is below what
+  // the FP32 eigenpairs reach by themselves
+  if (adapt_tol) refine = (*(volatile const double*)adapt_tol < kRefineBelow) ? 1 : 0;
   extern __shared__ float smj[];
   const int ld = Kp + 1;
   float* A = smj;                      // Kp x (Kp+1): T, then the Householder vectors
@@ -756,6 +764,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         float acc = 0.f;
         if (i < m) {
           const float* row = A + (size_t)(k + 1 + i) * ld + (k + 1);
+#pragma unroll 4
           for (int j = part; j < m; j += 4) acc = fmaf(row[j], v[j], acc);
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -780,12 +789,14 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
       } else {
         // the next trailing block (local rows and columns 1..m-1); local row 0
         // (the upper part of row k+1) is never read again
-        const int mm = m - 1;
-        for (int idx = tid - 32; idx < mm * mm; idx += nth - 32) {
-          const int i = 1 + idx / mm, j = 1 + idx % mm;
-          const float wi = pb[i] - kk * v[i], wj = pb[j] - kk * v[j];
-          float* a = &A[(k + 1 + i) * ld + (k + 1 + j)];
-          *a = fmaf(-v[i], wj, fmaf(-wi, v[j], *a));
+        for (int i = warp; i < m; i += nwarps - 1) {  // warps 1.. take rows 1, 2, ...
+          const float vi = v[i], wi = pb[i] - kk * vi;
+          float* arow = &A[(k + 1 + i) * ld + (k + 1)];
+#pragma unroll 2
+          for (int j = 1 + lane; j < m; j += 32) {
+            const float vj = v[j], wj = pb[j] - kk * vj;
+            arow[j] = fmaf(-vi, wj, fmaf(-wi, vj, arow[j]));
+          }
         }
       }
       __syncthreads();
@@ -960,14 +971,16 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         for (int q = a0; q < base + cc; ++q) {
           if (q >= base) warp_normalise(V, ld, K, q, lane, (unsigned long long)(q * 8 + it));
           if (act && b > q) {
-            float d0 = 0.f, d1 = 0.f;
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
             int i = 0;
-            for (; i + 1 < K; i += 2) {
-              d0 = fmaf(V[i * ld + b], V[i * ld + q], d0);
-              d1 = fmaf(V[(i + 1) * ld + b], V[(i + 1) * ld + q], d1);
+#pragma unroll 2
+            for (; i + 3 < K; i += 4) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) d[u] = fmaf(V[(i + u) * ld + b], V[(i + u) * ld + q], d[u]);
             }
-            if (i < K) d0 = fmaf(V[i * ld + b], V[i * ld + q], d0);
-            const float dot = d0 + d1;
+            for (; i < K; ++i) d[0] = fmaf(V[i * ld + b], V[i * ld + q], d[0]);
+            const float dot = (d[0] + d[1]) + (d[2] + d[3]);
+#pragma unroll 8
             for (int r = 0; r < K; ++r) V[r * ld + b] = fmaf(-dot, V[r * ld + q], V[r * ld + b]);
           }
           __syncwarp();
@@ -1051,20 +1064,30 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     for (int o = tid; o < K * nb; o += nth) {  // z = T y_j
       const int k = o / nb, jj = o % nb;
       const int col = K - 1 - (j0 + jj);
-      DF acc;
-      float lo = 0.f;
+      DF acc0, acc1;  // two interleaved halves of the sum
+      float lo0 = 0.f, lo1 = 0.f;
       const float* th = Th + k * ld;
-#pragma unroll 4
-      for (int l = 0; l < K; ++l) acc.fma_acc(th[l], V[l * ld + col]);
-      int pk = k * (k + 1) / 2;  // Tl(k, l) for l < k, then Tl(l, k) for l >= k
-      for (int l = 0; l < k; ++l) lo = fmaf(Tl[pk + l], V[l * ld + col], lo);
-      int pl = k * (k + 1) / 2 + k;
-      for (int l = k; l < K; ++l) {
-        lo = fmaf(Tl[pl], V[l * ld + col], lo);
-        pl += l + 1;
+      int l = 0;
+#pragma unroll 2
+      for (; l + 1 < K; l += 2) {
+        acc0.fma_acc(th[l], V[l * ld + col]);
+        acc1.fma_acc(th[l + 1], V[(l + 1) * ld + col]);
       }
-      Zh[k * JB + jj] = acc.hi;
-      Zl[k * JB + jj] = acc.lo + lo;
+      if (l < K) acc0.fma_acc(th[l], V[l * ld + col]);
+      const int pk = k * (k + 1) / 2;  // Tl(k, l) for l < k, then Tl(l, k) for l >= k
+#pragma unroll 4
+      for (int q = 0; q < k; ++q) lo0 = fmaf(Tl[pk + q], V[q * ld + col], lo0);
+      int pl = pk + k;
+      for (int q = k; q < K; ++q) {
+        lo1 = fmaf(Tl[pl], V[q * ld + col], lo1);
+        pl += q + 1;
+      }
+      // (hi0 + hi1) exactly as a pair, then the low parts
+      const float sh = acc0.hi + acc1.hi;
+      const float bb = sh - acc0.hi;
+      const float eh = (acc0.hi - (sh - bb)) + (acc1.hi - bb);
+      Zh[k * JB + jj] = sh;
+      Zl[k * JB + jj] = eh + acc0.lo + acc1.lo + lo0 + lo1;
     }
     __syncthreads();
     for (int jj = warp; jj < nb; jj += nwarps) {  // theta_j: FP64 Rayleigh quotient
@@ -1094,59 +1117,77 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     for (int o = tid; o < K * nb; o += nth) {  // e_ij = y_i^T r_j / (theta_j - lambda_i) (into Zl)
       const int i = o / nb, jj = o % nb;
       const int col = K - 1 - (j0 + jj);
-      float d0 = 0.f, d1 = 0.f;
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
       int k = 0;
 #pragma unroll 2
-      for (; k + 1 < K; k += 2) {
-        d0 = fmaf(V[k * ld + i], Zh[k * JB + jj], d0);
-        d1 = fmaf(V[(k + 1) * ld + i], Zh[(k + 1) * JB + jj], d1);
+      for (; k + 3 < K; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = fmaf(V[(k + u) * ld + i], Zh[(k + u) * JB + jj], d[u]);
       }
-      if (k < K) d0 = fmaf(V[k * ld + i], Zh[k * JB + jj], d0);
+      for (; k < K; ++k) d[0] = fmaf(V[k * ld + i], Zh[k * JB + jj], d[0]);
       const float gap = (float)lamj[jj] - dg[i];
-      Zl[i * JB + jj] = (i == col || fabsf(gap) <= delta) ? 0.f : (d0 + d1) / gap;
+      Zl[i * JB + jj] = (i == col || fabsf(gap) <= delta) ? 0.f : ((d[0] + d[1]) + (d[2] + d[3])) / gap;
     }
     __syncthreads();
     for (int o = tid; o < K * nb; o += nth) {  // y_j + Y e_j
       const int row = o / nb, jj = o % nb;
       const int col = K - 1 - (j0 + jj);
-      float a0 = V[row * ld + col], a1 = 0.f;
+      float a[4] = {V[row * ld + col], 0.f, 0.f, 0.f};
       int i = 0;
 #pragma unroll 2
-      for (; i + 1 < K; i += 2) {
-        a0 = fmaf(V[row * ld + i], Zl[i * JB + jj], a0);
-        a1 = fmaf(V[row * ld + i + 1], Zl[(i + 1) * JB + jj], a1);
+      for (; i + 3 < K; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fmaf(V[row * ld + i + u], Zl[(i + u) * JB + jj], a[u]);
       }
-      if (i < K) a0 = fmaf(V[row * ld + i], Zl[i * JB + jj], a0);
-      Yout[(size_t)(j0 + jj) * ldy + row] = a0 + a1;
+      for (; i < K; ++i) a[0] = fmaf(V[row * ld + i], Zl[i * JB + jj], a[0]);
+      Yout[(size_t)(j0 + jj) * ldy + row] = (a[0] + a[1]) + (a[2] + a[3]);
     }
     for (int jj = tid; jj < nb; jj += nth) theta[j0 + jj] = lamj[jj];
     __syncthreads();
   }
   // Symmetric orthonormality correction of the refined vectors (the first-
-  // order refinement leaves O(E^2) non-orthogonality): with G = Y^T Y from
+  // order correction leaves O(E^2) non-orthogonality): with G = Y^T Y from
   // FP32-pair sums, Y <- Y (3I - G) / 2, which maps G to I + O((G - I)^2).
-  // A (now free) holds I - G, V (now free) the corrected columns.
+  // The refined vectors are staged in A (K x nout), I - G in the refinement
+  // scratch (nout x nout), the corrected vectors in V.
+  float* Yr = A;    // Yr[row * nout + j]
+  float* IG = scr;  // (I - G)[i * nout + j]
+  for (int o = tid; o < K * nout; o += nth) {
+    const int j = o / K, row = o % K;
+    Yr[row * nout + j] = __ldcg(&Yout[(size_t)j * ldy + row]);
+  }
+  __syncthreads();
   for (int o = tid; o < nout * nout; o += nth) {
-    int i = o / nout, j = o % nout;
+    const int i = o / nout, j = o % nout;
     if (j < i) continue;
-    DF g;
-#pragma unroll 8
-    for (int k = 0; k < K; ++k) g.fma_acc(__ldcg(&Yout[(size_t)i * ldy + k]), __ldcg(&Yout[(size_t)j * ldy + k]));
-    float v = (float)((i == j ? 1.0 : 0.0) - g.value());
-    A[i * nout + j] = v;
-    A[j * nout + i] = v;
+    DF g0, g1;
+    int k = 0;
+#pragma unroll 2
+    for (; k + 1 < K; k += 2) {
+      g0.fma_acc(Yr[k * nout + i], Yr[k * nout + j]);
+      g1.fma_acc(Yr[(k + 1) * nout + i], Yr[(k + 1) * nout + j]);
+    }
+    if (k < K) g0.fma_acc(Yr[k * nout + i], Yr[k * nout + j]);
+    const float v = (float)((i == j ? 1.0 : 0.0) - (g0.value() + g1.value()));
+    IG[i * nout + j] = v;
+    IG[j * nout + i] = v;
   }
   __syncthreads();
   for (int o = tid; o < K * nout; o += nth) {
-    int row = o / nout, j = o % nout;
-    float corr = 0.f;
-#pragma unroll 8
-    for (int i = 0; i < nout; ++i) corr = fmaf(__ldcg(&Yout[(size_t)i * ldy + row]), A[i * nout + j], corr);
-    V[row * ld + j] = __ldcg(&Yout[(size_t)j * ldy + row]) + 0.5f * corr;
+    const int row = o / nout, j = o % nout;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    int i = 0;
+#pragma unroll 2
+    for (; i + 3 < nout; i += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] = fmaf(Yr[row * nout + i + u], IG[(i + u) * nout + j], c[u]);
+    }
+    for (; i < nout; ++i) c[0] = fmaf(Yr[row * nout + i], IG[i * nout + j], c[0]);
+    V[row * ld + j] = Yr[row * nout + j] + 0.5f * ((c[0] + c[1]) + (c[2] + c[3]));
   }
   __syncthreads();
   for (int o = tid; o < K * nout; o += nth) {
-    int row = o / nout, j = o % nout;
+    const int j = o / K, row = o % K;
     Yout[(size_t)j * ldy + row] = V[row * ld + j];
   }
 }
@@ -1166,9 +1207,9 @@ void init_lanczos_attributes() {
 }
 
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
-                    const int* skip, cudaStream_t st, int refine) {
+                    const int* skip, cudaStream_t st, int refine, const double* adapt_tol) {
   const int Kp = (K + 1) & ~1;
-  k_sym_eig<<<1, SE_THREADS, sym_eig_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, refine, skip);
+  k_sym_eig<<<1, SE_THREADS, sym_eig_smem(Kp), st>>>(T, K, Kp, theta, Y, ldy, nout, refine, adapt_tol, skip);
 }
 
 }  // namespace psdp
@@ -1270,10 +1311,12 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
   const int nr = max(0, min(rows, n - i0));
   const int rows4 = ((rows + 3) / 4) * 4;
   // stage my rows of Z (row-major) and of Q[:, :c0] (column-major); padding rows are zero
+#pragma unroll 4
   for (int idx = tid; idx < rows4 * W; idx += 256) {
     const int b = idx / rows4, i = idx % rows4;
     Zs[i * ldz + b] = (i < nr) ? __ldg(&src[(size_t)b * ldq + i0 + i]) : 0.f;
   }
+#pragma unroll 4
   for (int idx = tid; idx < rows4 * c0; idx += 256) {
     const int a = idx / rows4, i = idx % rows4;
     Qs[a * ldqs + i] = (i < nr) ? __ldg(&Q[(size_t)a * ldq + i0 + i]) : 0.f;
@@ -1295,6 +1338,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         const int ta = t / nTb, tb = t % nTb;
         float acc[4][4] = {};
         const int ib = p * rlen, ie = min(rows4, ib + rlen);
+#pragma unroll 4
         for (int i = ib; i < ie; ++i) {
           const float4 z = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
 #pragma unroll
@@ -1348,6 +1392,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
           acc[k][2] = z.z;
           acc[k][3] = z.w;
         }
+#pragma unroll 4
         for (int a = 0; a < c0; ++a) {
           const float4 q = *reinterpret_cast<const float4*>(&Qs[a * ldqs + 4 * ti]);
           const float4 h = *reinterpret_cast<const float4*>(&Hf[a * W + 4 * tb]);
@@ -1384,6 +1429,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         const int tb = ta + t;
         float acc[4][4] = {};
         const int ib = p * rlen, ie = min(rows4, ib + rlen);
+#pragma unroll 4
         for (int i = ib; i < ie; ++i) {
           const float4 za = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * ta]);
           const float4 zb = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
@@ -1486,17 +1532,18 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int l = j + lane + 32 * h;
-            float s0 = 0.f, s1 = 0.f;
+            float sa[4] = {0.f, 0.f, 0.f, 0.f};
             if (l < W) {
-              s0 = Gh[j * W + l];
+              sa[0] = Gh[j * W + l];
               int i = 0;
-              for (; i + 1 < j; i += 2) {
-                s0 = fmaf(-Gh[i * W + j], Gh[i * W + l], s0);
-                s1 = fmaf(-Gh[(i + 1) * W + j], Gh[(i + 1) * W + l], s1);
+#pragma unroll 2
+              for (; i + 3 < j; i += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sa[u] = fmaf(-Gh[(i + u) * W + j], Gh[(i + u) * W + l], sa[u]);
               }
-              if (i < j) s0 = fmaf(-Gh[i * W + j], Gh[i * W + l], s0);
+              for (; i < j; ++i) sa[0] = fmaf(-Gh[i * W + j], Gh[i * W + l], sa[0]);
             }
-            sv[h] = s0 + s1;
+            sv[h] = (sa[0] + sa[1]) + (sa[2] + sa[3]);
           }
           const float piv = __shfl_sync(0xffffffffu, sv[0], 0);
           const bool def = !(piv > kOrthDefTol);
@@ -1520,14 +1567,15 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
       for (int i = tid; i < nr; i += 256) {
         float* zr = Zs + i * ldz;
         for (int j = 0; j < W; ++j) {
-          float s0 = zr[j] * sc[j], s1 = 0.f;
+          float sa[4] = {zr[j] * sc[j], 0.f, 0.f, 0.f};
           int k = 0;
-          for (; k + 1 < j; k += 2) {
-            s0 = fmaf(-zr[k], Gh[k * W + j], s0);
-            s1 = fmaf(-zr[k + 1], Gh[(k + 1) * W + j], s1);
+#pragma unroll 2
+          for (; k + 3 < j; k += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sa[u] = fmaf(-zr[k + u], Gh[(k + u) * W + j], sa[u]);
           }
-          if (k < j) s0 = fmaf(-zr[k], Gh[k * W + j], s0);
-          float x = (s0 + s1) * rd[j];
+          for (; k < j; ++k) sa[0] = fmaf(-zr[k], Gh[k * W + j], sa[0]);
+          float x = ((sa[0] + sa[1]) + (sa[2] + sa[3])) * rd[j];
           if (fl[j]) x = hash_uniform(pseed, (unsigned long long)(i0 + i), (unsigned long long)(1000 + j));
           zr[j] = x;
         }

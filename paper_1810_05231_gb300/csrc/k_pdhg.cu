@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   for (int o = tid; o < RZ_RB * w; o += blockDim.x) {
     int i = o / w, t = o % w;
     float v = 0.f, u = 0.f;
+#pragma unroll 8
     for (int k = 0; k < K; ++k) {
       float y = Ys[k * w + t];
       v = fmaf(Qs[i * ldk + k], y, v);

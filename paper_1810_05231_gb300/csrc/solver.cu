@@ -305,7 +305,7 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
   }
   launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
   dbg(wk, "rr gram T", st);
-  launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st);
+  launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
   dbg(wk, "rr eig", st);
   int cycle_launches = 3 + s;  // Gram of T, eigensolver, Ritz; one product per step
   for (int j = 1; j <= s; ++j) cycle_launches += orth_cluster_applies(n, j * w, w) ? 1 : 11;
@@ -320,7 +320,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   const int use = in_graph ? 1 : 0;
   if (k.full) {
     launch_s_to_t(wk.S, wk.lds, n, wk.H, st);
-    launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, st);
+    launch_sym_eig(wk.H, n, wk.theta, wk.Y, kMaxK, n, nullptr, st, 1, &wk.ctl->lz_tol);
     launch_full_eig_factors(wk, n, st);
   } else {
     if (g_debug) g_debug_n = n;

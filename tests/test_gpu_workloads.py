@@ -1,0 +1,85 @@
+"""Whole solves of the larger synthetic workloads to the 1e-4 target, checked
+with certificates that do not depend on the iteration (Sec. 1.3 duality):
+primal feasibility on the row-scaled problem (reading A6), the relative
+duality gap, and dual feasibility lambda_min(C + M*(y)) >= -1e-4 (1 + ||C||_F)
+computed by a sparse Lanczos eigensolver (scipy) on the CPU.
+
+- sensor network localisation, 1000 sensors + 10 anchors (Sec. 5.2): C = 0,
+  exact distances; the recovered positions (the off-diagonal block of Z) are
+  compared with the true ones;
+- graph equipartition with the structured row tr(11^T X) = 0 on G(5000, 0.002)
+  (Sec. 5.1), the largest single-GPU configuration (n = 5000, S = 100 MB).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+import sdp_instances as si
+from oracle.sdp import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1810_05231_gb300 as p
+
+    return p
+
+
+def _dual_min_eig(prob, y_alg):
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    Z = prob.C + prob.M.adjoint(y_alg)
+    lam = sla.eigsh(Z, k=1, which="SA", tol=1e-9, maxiter=20000, return_eigenvectors=False)[0]
+    return float(lam) / (1.0 + np.linalg.norm(prob.C, "fro"))
+
+
+def _scaled_checks(inst, got):
+    prob = Problem.from_instance(inst)
+    sp, scale = oracle.normalize_rows(prob)
+    y_alg = -got["y"] / scale
+    MX = sp.M.apply(got["X"])
+    b = sp.rhs[: sp.m_eq]
+    primal = np.linalg.norm(MX[: sp.m_eq] - b) / (1.0 + np.linalg.norm(b))
+    pobj = float(np.sum(sp.C * got["X"]))
+    dobj = float(-sp.rhs @ y_alg)
+    gap = abs(pobj - dobj) / (1.0 + abs(pobj) + abs(dobj))
+    return sp, y_alg, primal, gap, pobj
+
+
+def test_sensor_network_1000(pkg):
+    inst = si.config_sensor_1000()
+    slv = pkg.Solver(tol=1e-4, rank_init=8, max_iter=50000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    got = slv.get_primal_dual()
+    sp, y_alg, primal, gap, _ = _scaled_checks(inst, got)
+    assert primal <= 1e-4 and gap <= 1e-4, (primal, gap)
+    assert _dual_min_eig(sp, y_alg) >= -1e-4
+    d = inst.meta["d"]
+    pos = got["X"][d:, :d]
+    rmse = float(np.sqrt(np.mean((pos - inst.meta["sensors"]) ** 2)))
+    assert rmse <= 1e-2, rmse
+    slv.close()
+
+
+def test_equipartition_5000(pkg):
+    inst = si.config_equipartition_5000()
+    slv = pkg.Solver(tol=1e-4, rank_init=8, max_iter=30000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    got = slv.get_primal_dual()
+    sp, y_alg, primal, gap, pobj = _scaled_checks(inst, got)
+    assert primal <= 1e-4 and gap <= 1e-4, (primal, gap)
+    assert abs(pobj - info.primal_obj) <= 1e-6 * (1 + abs(pobj))
+    assert _dual_min_eig(sp, y_alg) >= -1e-4
+    slv.close()
