@@ -564,7 +564,7 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
 constexpr int JB = 32;  // wanted columns refined per pass
 constexpr int SE_THREADS = 512;
 constexpr float kSePivmin = 1e-30f;   // Sturm pivots below this (unit-norm matrix) count as negative
-constexpr float kSeGroupTol = 1e-3f;  // inverse-iteration groups (unit-norm matrix)
+constexpr float kSeGroupTol = 2e-5f;  // inverse-iteration groups (unit-norm matrix)
 constexpr double kRefineBelow = 2e-5;  // adaptive refinement: Ritz residual tolerances below this
 
 // Numbers of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal)
@@ -1026,10 +1026,46 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     }
   }
   __syncthreads();
-  if (!refine) {  // the FP32 eigenpairs as they are, in descending order
+  if (!refine) {
+    // the FP32 eigenpairs in descending order, with one symmetric
+    // orthonormality correction Y <- Y (3I - G)/2, G = Y^T Y (inverse
+    // iteration leaves eigenvectors of eigenvalues closer than ~1e-3 ||T||
+    // apart non-orthogonal to O(eps ||T|| / gap); mixing inside such pairs
+    // changes V diag(lambda) V^T only by O(eps ||T||))
+    float* Yr = A;    // Yr[row * nout + j] (A is free after the back-transformation)
+    float* IG = scr;  // (I - G)[i * nout + j]
+    for (int o = tid; o < K * nout; o += nth) {
+      const int j = o % nout, row = o / nout;
+      Yr[row * nout + j] = V[row * ld + (K - 1 - j)];
+    }
+    __syncthreads();
+    for (int o = tid; o < nout * nout; o += nth) {
+      const int i = o / nout, j = o % nout;
+      if (j < i) continue;
+      float g[4] = {0.f, 0.f, 0.f, 0.f};
+      int k = 0;
+#pragma unroll 2
+      for (; k + 3 < K; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = fmaf(Yr[(k + u) * nout + i], Yr[(k + u) * nout + j], g[u]);
+      }
+      for (; k < K; ++k) g[0] = fmaf(Yr[k * nout + i], Yr[k * nout + j], g[0]);
+      const float v = (i == j ? 1.f : 0.f) - ((g[0] + g[1]) + (g[2] + g[3]));
+      IG[i * nout + j] = v;
+      IG[j * nout + i] = v;
+    }
+    __syncthreads();
     for (int o = tid; o < K * nout; o += nth) {
       const int j = o / K, row = o % K;
-      Yout[(size_t)j * ldy + row] = V[row * ld + (K - 1 - j)];
+      float c[4] = {0.f, 0.f, 0.f, 0.f};
+      int i = 0;
+#pragma unroll 2
+      for (; i + 3 < nout; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = fmaf(Yr[row * nout + i + u], IG[(i + u) * nout + j], c[u]);
+      }
+      for (; i < nout; ++i) c[0] = fmaf(Yr[row * nout + i], IG[i * nout + j], c[0]);
+      Yout[(size_t)j * ldy + row] = Yr[row * nout + j] + 0.5f * ((c[0] + c[1]) + (c[2] + c[3]));
     }
     for (int j = tid; j < nout; j += nth) theta[j] = (double)dg[K - 1 - j];
     return;

@@ -80,6 +80,21 @@ __device__ void reduce_partials(const double* part, int P, int stride, int L, do
 // ---------------------------------------------------------------------------
 // Ritz vectors V = Q Y, S V = W Y, residuals and the projection's stop test
 // ---------------------------------------------------------------------------
+struct DFc {
+  float hi, lo;
+  __device__ __forceinline__ DFc() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void fma_acc(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = fmaf(a, b, -p);
+    float s = __fadd_rn(hi, p);
+    float bb = __fsub_rn(s, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 constexpr int RZ_RB = 32;
 
 __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, int r, int s_steps, int cycle_launches,
@@ -116,17 +131,38 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   }
   for (int t = tid; t < w; t += blockDim.x) th[t] = wk.theta[t];
   __syncthreads();
-  for (int o = tid; o < RZ_RB * w; o += blockDim.x) {
-    int i = o / w, t = o % w;
-    float v = 0.f, u = 0.f;
-#pragma unroll 8
+  {  // V = Q Y and W Y on this CTA's rows: 2 rows x (w/16) columns per thread
+    const int ti = tid >> 4, tt = tid & 15;  // rows ti, ti + 16; columns tt + 16 j
+    const int wg = (w + 15) / 16;
+    float v[2][4] = {}, u[2][4] = {};
+    const float* q0 = Qs + ti * ldk;
+    const float* q1 = Qs + (ti + 16) * ldk;
+    const float* w0 = Ws + ti * ldk;
+    const float* w1 = Ws + (ti + 16) * ldk;
+#pragma unroll 2
     for (int k = 0; k < K; ++k) {
-      float y = Ys[k * w + t];
-      v = fmaf(Qs[i * ldk + k], y, v);
-      u = fmaf(Ws[i * ldk + k], y, u);
+      const float a0 = q0[k], a1 = q1[k], b0 = w0[k], b1 = w1[k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j < wg) {
+          const float y = Ys[k * w + min(tt + 16 * j, w - 1)];
+          v[0][j] = fmaf(a0, y, v[0][j]);
+          v[1][j] = fmaf(a1, y, v[1][j]);
+          u[0][j] = fmaf(b0, y, u[0][j]);
+          u[1][j] = fmaf(b1, y, u[1][j]);
+        }
+      }
     }
-    Vs[i * (w + 1) + t] = v;
-    WVs[i * (w + 1) + t] = u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = tt + 16 * j;
+      if (j < wg && t < w) {
+        Vs[ti * (w + 1) + t] = v[0][j];
+        Vs[(ti + 16) * (w + 1) + t] = v[1][j];
+        WVs[ti * (w + 1) + t] = u[0][j];
+        WVs[(ti + 16) * (w + 1) + t] = u[1][j];
+      }
+    }
   }
   __syncthreads();
   // in-place write-back (each CTA owns its rows), row-major copy of V
@@ -147,21 +183,22 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   }
   // partial sums per Ritz column: ||wv - theta v||^2, v.wv, v.v, sum v
   double* part = wk.ritz_part + (size_t)blockIdx.x * 4 * w;
-  for (int t = tid; t < w; t += blockDim.x) {
-    double a = 0, b = 0, c = 0, d = 0;
+  for (int t = tid; t < w; t += blockDim.x) {  // FP32 pairs over this CTA's rows
+    DFc b, c, d;
+    float a = 0.f;
     float tht = (float)th[t];
     for (int i = 0; i < rows; ++i) {
       float v = Vs[i * (w + 1) + t], u = WVs[i * (w + 1) + t];
       float res = fmaf(-tht, v, u);
-      a += (double)res * res;
-      b += (double)v * u;
-      c += (double)v * v;
-      d += (double)v;
+      a = fmaf(res, res, a);
+      b.fma_acc(v, u);
+      c.fma_acc(v, v);
+      d.fma_acc(v, 1.f);  // column sums enter (1^T v)^2 of structured rows: keep them exact
     }
-    part[t] = a;
-    part[w + t] = b;
-    part[2 * w + t] = c;
-    part[3 * w + t] = d;
+    part[t] = (double)a;
+    part[w + t] = b.value();
+    part[2 * w + t] = c.value();
+    part[3 * w + t] = d.value();
   }
   if (!last_block(&wk.counters[CNT_RITZ * 512])) return;
   // final reduction in block order
@@ -454,20 +491,6 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
 // the last block to finish, by the controller.
 constexpr int GC_T = 16, GC_RC = 128;
 
-struct DFc {
-  float hi, lo;
-  __device__ __forceinline__ DFc() : hi(0.f), lo(0.f) {}
-  __device__ __forceinline__ void fma_acc(float a, float b) {
-    float p = __fmul_rn(a, b);
-    float e = fmaf(a, b, -p);
-    float s = __fadd_rn(hi, p);
-    float bb = __fsub_rn(s, hi);
-    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    hi = s;
-    lo = __fadd_rn(lo, __fadd_rn(err, e));
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
 
 __global__ void __launch_bounds__(256) k_gram_control(DevProblem pb, DevWork wk, int act, int rows_per_split,
                                                       int iter_launches, cudaGraphConditionalHandle cond,
