@@ -283,6 +283,9 @@ def cpu_oracle_sample(seconds=15.0, min_iters=2):
 
 def run_mimo_batch(args):
     """Aggregate solves/s of the MIMO batch (row a12), inputs resident."""
+    # more hardware work queues than the default 8, so that the instances'
+    # streams do not share queues (set before the first CUDA call)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
 
     import paper_1810_05231_gb300 as pkg
@@ -298,7 +301,7 @@ def run_mimo_batch(args):
         return out
     for _ in range(max(1, args.warmup)):
         sv = make()
-        pkg.solve_batch(sv, host_threads=16)
+        pkg.solve_batch(sv, host_threads=args.host_threads)
         for s in sv:
             s.close()
     times, infos = [], None
@@ -306,7 +309,7 @@ def run_mimo_batch(args):
         sv = make()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        infos = pkg.solve_batch(sv, host_threads=16)
+        infos = pkg.solve_batch(sv, host_threads=args.host_threads)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         for s in sv:
@@ -317,7 +320,7 @@ def run_mimo_batch(args):
             "value": round(len(insts) / t, 3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(1000 * t, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "mimo_batch_256_seed4", "host_threads": 16, "tol": 1e-4},
+            "config": {"workload": "mimo_batch_256_seed4", "host_threads": args.host_threads, "tol": 1e-4},
             "converged": conv, "iters_total": int(sum(i.iters for i in infos)),
             "max_iters": int(max(i.iters for i in infos))}
     print(json.dumps(line))
@@ -334,6 +337,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"])
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--host-threads", type=int, default=48)
     args = ap.parse_args()
     if args.workload == "mimo-batch":
         return run_mimo_batch(args)

@@ -567,6 +567,19 @@ constexpr float kSePivmin = 1e-30f;   // Sturm pivots below this (unit-norm matr
 constexpr float kSeGroupTol = 2e-5f;  // inverse-iteration groups (unit-norm matrix)
 constexpr double kRefineBelow = 2e-5;  // adaptive refinement: Ritz residual tolerances below this
 
+// Number of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal) below x.
+__device__ __forceinline__ int sturm_count(const float* d, const float* e2, int K, float x) {
+  float q = d[0] - x;
+  if (fabsf(q) < kSePivmin) q = -kSePivmin;
+  int c = (q < 0.f);
+  for (int i = 1; i < K; ++i) {
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < kSePivmin) q = -kSePivmin;
+    c += (q < 0.f);
+  }
+  return c;
+}
+
 // Numbers of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal)
 // below x0 and below x1 (two interleaved Sturm sequences).
 __device__ __forceinline__ void sturm_count2(const float* d, const float* e2, int K, float x0, float x1,
@@ -643,6 +656,77 @@ __device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
 #pragma unroll 4
   for (int i = K - 2; i >= 0; --i) {
     const float xi = (x[i * ld] - f.u1[i] * x1 - f.u2[i] * x2) * f.u0[i];
+    x[i * ld] = xi;
+    x2 = x1;
+    x1 = xi;
+  }
+}
+
+// The same factorisation stored compactly in shared memory, one slot per
+// thread (slot-interleaved arrays: entry i of slot s at i * ns + s): the
+// multiplier l_i, the reciprocal pivot of row i and the swap bit.  The rest
+// of U is rebuilt from d, e and lam during the solve: a swapped row i is
+// (e_i, d_{i+1} - lam, e_{i+1}); an unswapped row is (p0_i, p1_i, 0) with
+// p1_i = e_i after an unswapped row (or at i = 0) and -l_{i-1} e_i after a
+// swapped one.
+__device__ void tri_lu_slot(const float* d, const float* e, int K, float lam, float tiny, float* lm, float* rp,
+                            unsigned* sw, int ns, int s) {
+  float p0 = d[0] - lam, p1 = (K > 1) ? e[0] : 0.f;
+  for (int w = 0; w < (K + 31) / 32; ++w) sw[w * ns + s] = 0u;
+  unsigned bits = 0u;
+  for (int i = 0; i < K - 1; ++i) {
+    const float s0 = e[i], s1 = d[i + 1] - lam, s2 = (i + 2 < K) ? e[i + 1] : 0.f;
+    float l;
+    if (fabsf(p0) >= fabsf(s0)) {
+      if (p0 == 0.f) p0 = tiny;
+      l = s0 / p0;
+      rp[i * ns + s] = 1.f / p0;
+      p0 = s1 - l * p1;
+      p1 = s2;
+    } else {
+      l = p0 / s0;
+      rp[i * ns + s] = 1.f / s0;
+      bits |= 1u << (i & 31);
+      p0 = p1 - l * s1;
+      p1 = -l * s2;
+    }
+    lm[i * ns + s] = l;
+    if ((i & 31) == 31 || i == K - 2) {  // flush a full word, or the last one
+      sw[(i >> 5) * ns + s] = bits;
+      bits = 0u;
+    }
+  }
+  rp[(K - 1) * ns + s] = 1.f / ((p0 == 0.f) ? tiny : p0);
+}
+
+__device__ void tri_solve_slot(const float* d, const float* e, int K, float lam, const float* lm, const float* rp,
+                               const unsigned* sw, int ns, int s, float* x, int ld) {
+  float a = x[0];
+#pragma unroll 4
+  for (int i = 0; i < K - 1; ++i) {
+    float b = x[(i + 1) * ld];
+    if ((sw[(i >> 5) * ns + s] >> (i & 31)) & 1u) {
+      const float t = a;
+      a = b;
+      b = t;
+    }
+    x[i * ld] = a;
+    a = fmaf(-lm[i * ns + s], a, b);
+  }
+  float x2 = 0.f, x1 = a * rp[(K - 1) * ns + s];
+  x[(K - 1) * ld] = x1;
+  for (int i = K - 2; i >= 0; --i) {
+    const bool swp = (sw[(i >> 5) * ns + s] >> (i & 31)) & 1u;
+    float u1, u2;
+    if (swp) {
+      u1 = d[i + 1] - lam;
+      u2 = (i + 2 < K) ? e[i + 1] : 0.f;
+    } else {
+      const bool prev_swp = (i > 0) && ((sw[((i - 1) >> 5) * ns + s] >> ((i - 1) & 31)) & 1u);
+      u1 = prev_swp ? -lm[(i - 1) * ns + s] * e[i] : e[i];
+      u2 = 0.f;
+    }
+    const float xi = (x[i * ld] - u1 * x1 - u2 * x2) * rp[i * ns + s];
     x[i * ld] = xi;
     x2 = x1;
     x1 = xi;
@@ -763,9 +847,14 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         const int i = tid >> 2, part = tid & 3;
         float acc = 0.f;
         if (i < m) {
+          // blocks of 8 columns, 32 apart: the 32 lanes (8 rows x 4 parts)
+          // then touch 32 different banks (ld is 1 mod 32... or odd)
           const float* row = A + (size_t)(k + 1 + i) * ld + (k + 1);
-#pragma unroll 4
-          for (int j = part; j < m; j += 4) acc = fmaf(row[j], v[j], acc);
+          for (int jb = 8 * part; jb < m; jb += 32) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (jb + u < m) acc = fmaf(row[jb + u], v[jb + u], acc);
+          }
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -847,16 +936,21 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
   }
   __syncthreads();
 
-  // ---- (2) eigenvalues: slicing pass (two points per thread), then multisection
+  // ---- (2) eigenvalues: slicing pass (one point per thread), then
+  // multisection of the wanted eigenvalues only (a >= a_need: the nout
+  // largest, or all of them when the vectors are refined)
+  const int a_need = refine ? 0 : max(0, K - nout);
   const float gl = s_gl, gu = s_gu;
-  const int P = 2 * nth;
+  const int P = nth;
   {
-    const float x0 = gl + (gu - gl) * (float)(2 * tid + 1) / (float)(P + 1);
-    const float x1 = gl + (gu - gl) * (float)(2 * tid + 2) / (float)(P + 1);
+    const float x0 = gl + (gu - gl) * (float)(tid + 1) / (float)(P + 1);
+    const float x1 = gl + (gu - gl) * (float)(((tid + nth / 2) % nth) + 1) / (float)(P + 1);
     int c0, c1;
-    sturm_count2(td, te2, K, x0, x1, c0, c1);
-    slice[2 * tid] = c0;
-    slice[2 * tid + 1] = c1;
+    if (tid < nth / 2) {  // two interleaved sequences per thread of the lower half
+      sturm_count2(td, te2, K, x0, x1, c0, c1);
+      slice[tid] = c0;
+      slice[tid + nth / 2] = c1;
+    }
   }
   __syncthreads();
   for (int a = tid; a < K; a += nth) {  // bracket of the a-th smallest eigenvalue
@@ -873,29 +967,25 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
   }
   __syncthreads();
   {
-    const int G = nth / K;  // threads per eigenvalue (>= 4 for K <= 128)
-    const int NP = 2 * G;   // points per eigenvalue and step
-    const int a = tid / G, g = tid % G;
+    const int nw = K - a_need;
+    const int G = nth / nw;  // threads (= points) per wanted eigenvalue, >= 4
+    const int a = a_need + tid / G, g = tid % G;
     const bool act = a < K;
     float lo = act ? blo[a] : 0.f, hi = act ? bhi[a] : 0.f;
     int steps = 0;
-    for (long span = 1; span < 65536; span *= (NP + 1)) ++steps;
+    for (long span = 1; span < 32768; span *= (G + 1)) ++steps;
     for (int st = 0; st < steps; ++st) {
       int* f = flg + (st & 1) * 2 * SE_THREADS;
       if (act) {
-        const float x0 = lo + (hi - lo) * (float)(2 * g + 1) / (float)(NP + 1);
-        const float x1 = lo + (hi - lo) * (float)(2 * g + 2) / (float)(NP + 1);
-        int c0, c1;
-        sturm_count2(td, te2, K, x0, x1, c0, c1);
-        f[a * NP + 2 * g] = (c0 <= a) ? 1 : 0;
-        f[a * NP + 2 * g + 1] = (c1 <= a) ? 1 : 0;
+        const float x = lo + (hi - lo) * (float)(g + 1) / (float)(G + 1);
+        f[(a - a_need) * G + g] = (sturm_count(td, te2, K, x) <= a) ? 1 : 0;
       }
       __syncthreads();
       if (act) {
         float nlo = lo, nhi = hi;
-        for (int q = 0; q < NP; ++q) {
-          const float x = lo + (hi - lo) * (float)(q + 1) / (float)(NP + 1);
-          if (f[a * NP + q]) nlo = fmaxf(nlo, x);
+        for (int q = 0; q < G; ++q) {
+          const float x = lo + (hi - lo) * (float)(q + 1) / (float)(G + 1);
+          if (f[(a - a_need) * G + q]) nlo = fmaxf(nlo, x);
           else nhi = fminf(nhi, x);
         }
         lo = nlo;
@@ -906,6 +996,10 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
       blo[a] = 0.5f * (lo + hi);  // scaled eigenvalue
       dg[a] = 0.5f * (lo + hi) * tn;
     }
+    for (int b = tid; b < a_need; b += nth) {  // unwanted: the bracket's midpoint
+      blo[b] = 0.5f * (blo[b] + bhi[b]);
+      dg[b] = blo[b] * tn;
+    }
   }
   __syncthreads();
 
@@ -913,44 +1007,56 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
   // Only the eigenvalues a >= a_need are wanted (all with refinement); groups
   // of eigenvalues closer than kSeGroupTol are handled by one warp each.
   const float* lam = blo;
-  const int a_need = refine ? 0 : max(0, K - nout);
   if (tid == 0) {
     int ng = 0;
-    for (int a = 0; a < K;) {
+    for (int a = 0; a < a_need; ++a) gsz[a] = 0;
+    for (int a = a_need; a < K;) {
       int last = a;
       while (last + 1 < K && lam[last + 1] - lam[last] <= kSeGroupTol) ++last;
       gsz[a] = last - a + 1;
       for (int b = a + 1; b <= last; ++b) gsz[b] = 0;
-      if (last > a && last >= a_need) glist[ng++] = a;
+      if (last > a) glist[ng++] = a;
       a = last + 1;
     }
     s_ng = ng;
   }
   __syncthreads();
-  if (tid < K && tid >= a_need && gsz[tid] == 1) {  // isolated: one thread, three solves
-    const int b = tid;
-    TriLU f;
-    tri_lu(td, te, K, lam[b], 1.2e-7f, f);
-    float* x = V + b;  // column b, stride ld
-    for (int i = 0; i < K; ++i) x[i * ld] = hash_uniform(0x5EEDULL + (unsigned long long)b, (unsigned long long)i, 77ULL);
-    for (int it = 0; it < 3; ++it) {
-      tri_solve(f, K, x, ld);
-      float mx = 0.f;
-      for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(x[i * ld]));
-      if (!(mx > 0.f) || !(mx < 3e38f)) {
+  {  // isolated eigenvalues: one thread each, three solves; LU factors in
+     // shared-memory slots (the refinement scratch), in batches of ns
+    const int nwords = (K + 31) / 32;
+    const int ns = min(nth, (int)((Kp * (Kp + 1) / 2 + 2 * Kp * JB) / (2 * K + nwords)));
+    float* lm = scr;
+    float* rp = lm + (size_t)K * ns;
+    unsigned* swb = reinterpret_cast<unsigned*>(rp + (size_t)K * ns);
+    for (int b0 = a_need; b0 < K; b0 += ns) {
+      const int b = b0 + tid;
+      if (tid < ns && b < K && gsz[b] == 1) {
+        tri_lu_slot(td, te, K, lam[b], 1.2e-7f, lm, rp, swb, ns, tid);
+        float* x = V + b;  // column b, stride ld
         for (int i = 0; i < K; ++i)
-          x[i * ld] = hash_uniform(0xBADULL + (unsigned long long)(b * 8 + it), (unsigned long long)i, 78ULL);
-        continue;
+          x[i * ld] = hash_uniform(0x5EEDULL + (unsigned long long)b, (unsigned long long)i, 77ULL);
+        for (int it = 0; it < 3; ++it) {
+          tri_solve_slot(td, te, K, lam[b], lm, rp, swb, ns, tid, x, ld);
+          float mx = 0.f;
+          for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(x[i * ld]));
+          if (!(mx > 0.f) || !(mx < 3e38f)) {
+            for (int i = 0; i < K; ++i)
+              x[i * ld] = hash_uniform(0xBADULL + (unsigned long long)(b * 8 + it), (unsigned long long)i, 78ULL);
+            continue;
+          }
+          float ss = 0.f;
+          const float im = 1.f / mx;
+#pragma unroll 4
+          for (int i = 0; i < K; ++i) {
+            const float v = x[i * ld] * im;
+            x[i * ld] = v;
+            ss = fmaf(v, v, ss);
+          }
+          const float is = rsqrtf(ss);
+#pragma unroll 4
+          for (int i = 0; i < K; ++i) x[i * ld] *= is;
+        }
       }
-      float ss = 0.f;
-      const float im = 1.f / mx;
-      for (int i = 0; i < K; ++i) {
-        const float v = x[i * ld] * im;
-        x[i * ld] = v;
-        ss = fmaf(v, v, ss);
-      }
-      const float is = rsqrtf(ss);
-      for (int i = 0; i < K; ++i) x[i * ld] *= is;
     }
   }
   for (int gi = warp; gi < s_ng; gi += nwarps) {  // groups: lane = member, MGS in member order
@@ -1055,8 +1161,8 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
       IG[j * nout + i] = v;
     }
     __syncthreads();
-    for (int o = tid; o < K * nout; o += nth) {
-      const int j = o / K, row = o % K;
+    for (int o = tid; o < K * nout; o += nth) {  // consecutive threads: consecutive j (no bank conflicts)
+      const int row = o / nout, j = o % nout;
       float c[4] = {0.f, 0.f, 0.f, 0.f};
       int i = 0;
 #pragma unroll 2
@@ -1065,7 +1171,12 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         for (int u = 0; u < 4; ++u) c[u] = fmaf(Yr[row * nout + i + u], IG[(i + u) * nout + j], c[u]);
       }
       for (; i < nout; ++i) c[0] = fmaf(Yr[row * nout + i], IG[i * nout + j], c[0]);
-      Yout[(size_t)j * ldy + row] = Yr[row * nout + j] + 0.5f * ((c[0] + c[1]) + (c[2] + c[3]));
+      V[row * ld + j] = Yr[row * nout + j] + 0.5f * ((c[0] + c[1]) + (c[2] + c[3]));
+    }
+    __syncthreads();
+    for (int o = tid; o < K * nout; o += nth) {
+      const int j = o / K, row = o % K;
+      Yout[(size_t)j * ldy + row] = V[row * ld + j];
     }
     for (int j = tid; j < nout; j += nth) theta[j] = (double)dg[K - 1 - j];
     return;
@@ -1189,7 +1300,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
   float* Yr = A;    // Yr[row * nout + j]
   float* IG = scr;  // (I - G)[i * nout + j]
   for (int o = tid; o < K * nout; o += nth) {
-    const int j = o / K, row = o % K;
+    const int row = o / nout, j = o % nout;
     Yr[row * nout + j] = __ldcg(&Yout[(size_t)j * ldy + row]);
   }
   __syncthreads();
