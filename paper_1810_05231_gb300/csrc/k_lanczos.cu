@@ -1387,7 +1387,7 @@ constexpr float kOrthDefTol = 1e-5f;
 constexpr float kOrthNsTol = 0.1f;
 
 struct OrthLayout {
-  int rows, ldz, ldqs, c0;
+  int rows, ldr, ldqs, c0;
   size_t zs, qs, tmp, ph, pg, hf, gd, rf, total;  // byte offsets
 };
 
@@ -1395,16 +1395,15 @@ __host__ __device__ inline OrthLayout orth_layout(int rows, int c0, int W) {
   OrthLayout L;
   L.rows = rows;
   L.c0 = c0;
-  L.ldz = W + 4;
+  L.ldr = ((rows + 3) / 4) * 4 + 1;  // column-major Z: odd stride, row-per-thread access conflict-free
   L.ldqs = ((rows + 3) / 4) * 4 + 4;
-  const int rows4 = ((rows + 3) / 4) * 4;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
     o += (bytes + 15) & ~size_t(15);
     return at;
   };
-  L.zs = take((size_t)rows4 * L.ldz * 4);
+  L.zs = take((size_t)W * L.ldr * 4);
   L.qs = take((size_t)(c0 > 0 ? c0 : 1) * L.ldqs * 4);
   L.tmp = take(8192 * 4);  // split-row partial tiles: <= max(c0*W, 3*48*48, 7*32*32, 25*16*16) floats
   L.ph = take((size_t)(c0 > 0 ? c0 : 1) * W * 4);
@@ -1453,7 +1452,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
   __shared__ int fl[W];
   __shared__ unsigned s_dev;  // max |G - I| as float bits (non-negative)
   const int tid = threadIdx.x;
-  const int ldz = L.ldz, ldqs = L.ldqs;
+  const int ldr = L.ldr, ldqs = L.ldqs;
   const int i0 = rank * rows;
   const int nr = max(0, min(rows, n - i0));
   const int rows4 = ((rows + 3) / 4) * 4;
@@ -1461,7 +1460,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
 #pragma unroll 4
   for (int idx = tid; idx < rows4 * W; idx += 256) {
     const int b = idx / rows4, i = idx % rows4;
-    Zs[i * ldz + b] = (i < nr) ? __ldg(&src[(size_t)b * ldq + i0 + i]) : 0.f;
+    Zs[b * ldr + i] = (i < nr) ? __ldg(&src[(size_t)b * ldq + i0 + i]) : 0.f;
   }
 #pragma unroll 4
   for (int idx = tid; idx < rows4 * c0; idx += 256) {
@@ -1487,7 +1486,8 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         const int ib = p * rlen, ie = min(rows4, ib + rlen);
 #pragma unroll 4
         for (int i = ib; i < ie; ++i) {
-          const float4 z = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
+          const float4 z = make_float4(Zs[(4 * tb) * ldr + i], Zs[(4 * tb + 1) * ldr + i],
+                                       Zs[(4 * tb + 2) * ldr + i], Zs[(4 * tb + 3) * ldr + i]);
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const float q = Qs[(4 * ta + k) * ldqs + i];
@@ -1533,11 +1533,8 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         float acc[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          const float4 z = *reinterpret_cast<const float4*>(&Zs[(4 * ti + k) * ldz + 4 * tb]);
-          acc[k][0] = z.x;
-          acc[k][1] = z.y;
-          acc[k][2] = z.z;
-          acc[k][3] = z.w;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[k][u] = Zs[(4 * tb + u) * ldr + 4 * ti + k];
         }
 #pragma unroll 4
         for (int a = 0; a < c0; ++a) {
@@ -1554,8 +1551,8 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          *reinterpret_cast<float4*>(&Zs[(4 * ti + k) * ldz + 4 * tb]) =
-              make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Zs[(4 * tb + u) * ldr + 4 * ti + k] = acc[k][u];
       }
       __syncthreads();
     }
@@ -1578,8 +1575,10 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         const int ib = p * rlen, ie = min(rows4, ib + rlen);
 #pragma unroll 4
         for (int i = ib; i < ie; ++i) {
-          const float4 za = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * ta]);
-          const float4 zb = *reinterpret_cast<const float4*>(&Zs[i * ldz + 4 * tb]);
+          const float4 za = make_float4(Zs[(4 * ta) * ldr + i], Zs[(4 * ta + 1) * ldr + i],
+                                        Zs[(4 * ta + 2) * ldr + i], Zs[(4 * ta + 3) * ldr + i]);
+          const float4 zb = make_float4(Zs[(4 * tb) * ldr + i], Zs[(4 * tb + 1) * ldr + i],
+                                        Zs[(4 * tb + 2) * ldr + i], Zs[(4 * tb + 3) * ldr + i]);
           const float av[4] = {za.x, za.y, za.z, za.w};
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -1655,7 +1654,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
 #pragma unroll
         for (int l = 0; l < W; ++l) y[l] = 0.f;
         for (int k = 0; k < W; ++k) {
-          const float zk = Zs[i * ldz + k];
+          const float zk = Zs[k * ldr + i];
 #pragma unroll
           for (int m = 0; m < W / 4; ++m) {
             const float4 x = *reinterpret_cast<const float4*>(&X[k * W + 4 * m]);
@@ -1667,7 +1666,8 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
         }
 #pragma unroll
         for (int m = 0; m < W / 4; ++m)
-          *reinterpret_cast<float4*>(&Zs[i * ldz + 4 * m]) = make_float4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Zs[(4 * m + u) * ldr + i] = y[4 * m + u];
       }
     } else {
       // ---- Cholesky of the unit-diagonal Gram matrix by warp 0 (Crout order,
@@ -1712,19 +1712,19 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
       // ---- Z <- Z D^{-1/2} R^{-1} by forward substitution, one row per thread
       // (x_j = (z_j - sum_{k<j} x_k R_kj) / R_jj; dependent columns get pseudo-random entries)
       for (int i = tid; i < nr; i += 256) {
-        float* zr = Zs + i * ldz;
+        float* zr = Zs + i;  // column-major: entry k of this row at zr[k * ldr]
         for (int j = 0; j < W; ++j) {
-          float sa[4] = {zr[j] * sc[j], 0.f, 0.f, 0.f};
+          float sa[4] = {zr[j * ldr] * sc[j], 0.f, 0.f, 0.f};
           int k = 0;
 #pragma unroll 2
           for (; k + 3 < j; k += 4) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sa[u] = fmaf(-zr[k + u], Gh[(k + u) * W + j], sa[u]);
+            for (int u = 0; u < 4; ++u) sa[u] = fmaf(-zr[(k + u) * ldr], Gh[(k + u) * W + j], sa[u]);
           }
-          for (; k < j; ++k) sa[0] = fmaf(-zr[k], Gh[k * W + j], sa[0]);
+          for (; k < j; ++k) sa[0] = fmaf(-zr[k * ldr], Gh[k * W + j], sa[0]);
           float x = ((sa[0] + sa[1]) + (sa[2] + sa[3])) * rd[j];
           if (fl[j]) x = hash_uniform(pseed, (unsigned long long)(i0 + i), (unsigned long long)(1000 + j));
-          zr[j] = x;
+          zr[j * ldr] = x;
         }
       }
     }
@@ -1732,7 +1732,7 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
   }
   for (int idx = tid; idx < nr * W; idx += 256) {
     const int b = idx / nr, i = idx % nr;
-    Q[(size_t)(c0 + b) * ldq + i0 + i] = Zs[i * ldz + b];
+    Q[(size_t)(c0 + b) * ldq + i0 + i] = Zs[b * ldr + i];
   }
   cluster.sync();  // no CTA exits while another may still read its shared memory
 }
