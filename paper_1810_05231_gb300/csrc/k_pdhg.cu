@@ -61,8 +61,10 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
 // share one output, thread j of a group adding blocks j, j+g, ... in order,
 // the group combining with a fixed shuffle tree (deterministic).
 __device__ void reduce_partials(const double* part, int P, int stride, int L, double* out) {
+  // g threads per entry (power of two <= 32), each summing every g-th
+  // partial; more than one pass over the entries when L * g > blockDim
   int g = 1;
-  while (g < 32 && 2 * g * L <= (int)blockDim.x) g *= 2;
+  while (g < 32 && 4 * g <= P && g * L < 4 * (int)blockDim.x) g *= 2;
   const int per_pass = blockDim.x / g;
   for (int i0 = 0; i0 < L; i0 += per_pass) {
     const int i = i0 + (int)threadIdx.x / g, j = threadIdx.x % g;
@@ -212,23 +214,25 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     fin[3 * kMaxW + t] = fin4[3 * w + t];
   }
   __syncthreads();
+  __shared__ double rres[kMaxW];
+  for (int t = tid; t < w; t += blockDim.x) {  // one column per thread
+    double vv = fin[2 * kMaxW + t];
+    double lam = vv > 0.0 ? fin[kMaxW + t] / vv : th[t];  // Rayleigh quotient (FP64 sums)
+    wk.lam[nw][t] = lam;
+    wk.colsum[nw][t] = fin[3 * kMaxW + t];
+    rres[t] = sqrt(fin[t] / (vv > 0.0 ? vv : 1.0));
+  }
+  for (int t = w + tid; t < wk.ldv; t += blockDim.x) {
+    wk.lam[nw][t] = 0.0;
+    wk.colsum[nw][t] = 0.0;
+  }
+  __syncthreads();
   if (tid == 0) {
     double scale = 0.0;
     for (int t = 0; t < w; ++t) scale = fmax(scale, fabs(th[t]));
     if (scale == 0.0) scale = 1.0;
     double worst = 0.0;
-    for (int t = 0; t < w; ++t) {
-      double vv = fin[2 * kMaxW + t];
-      double lam = vv > 0.0 ? fin[kMaxW + t] / vv : th[t];  // Rayleigh quotient (FP64 sums)
-      wk.lam[nw][t] = lam;
-      wk.colsum[nw][t] = fin[3 * kMaxW + t];
-      double res = sqrt(fin[t] / (vv > 0.0 ? vv : 1.0));
-      if (t < r) worst = fmax(worst, res / scale);
-    }
-    for (int t = w; t < wk.ldv; ++t) {
-      wk.lam[nw][t] = 0.0;
-      wk.colsum[nw][t] = 0.0;
-    }
+    for (int t = 0; t < r; ++t) worst = fmax(worst, rres[t] / scale);
     ctl->lz_res = worst;
     ctl->lz_cycle += 1;
     ctl->lz_cycles_total += 1;
