@@ -845,17 +845,20 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     if (tk != 0.f) {  // uniform
       {  // p = tau A22 v: four threads per row
         const int i = tid >> 2, part = tid & 3;
-        float acc = 0.f;
+        float acc = 0.f, acc1 = 0.f;
         if (i < m) {
           // blocks of 8 columns, 32 apart: the 32 lanes (8 rows x 4 parts)
-          // then touch 32 different banks (ld is 1 mod 32... or odd)
+          // then touch 32 different banks
           const float* row = A + (size_t)(k + 1 + i) * ld + (k + 1);
           for (int jb = 8 * part; jb < m; jb += 32) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
+            for (int u = 0; u < 8; u += 2) {
               if (jb + u < m) acc = fmaf(row[jb + u], v[jb + u], acc);
+              if (jb + u + 1 < m) acc1 = fmaf(row[jb + u + 1], v[jb + u + 1], acc1);
+            }
           }
         }
+        acc += acc1;
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (i < m && part == 0) pb[i] = tk * acc;
@@ -866,15 +869,53 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
       for (int i = lane; i < m; i += 32) pv = fmaf(pb[i], v[i], pv);
       const float kk = 0.5f * tk * warp_sum_f(pv);
       if (warp == 0) {
-        // column k+1 (local column 0) first, then the next Householder vector
+        // column k+1 (local column 0), kept in registers (m <= 127: four rows
+        // per lane), and from it the next Householder vector in the same pass
         const float v0 = v[0], w0 = pb[0] - kk * v0;
-        for (int i = lane; i < m; i += 32) {
-          const float wi = pb[i] - kk * v[i];
-          float* a = &A[(k + 1 + i) * ld + (k + 1)];
-          *a = fmaf(-v[i], w0, fmaf(-wi, v0, *a));
+        float nv[4];
+        float ss = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int i = lane + 32 * q;
+          nv[q] = 0.f;
+          if (i < m) {
+            const float wi = pb[i] - kk * v[i];
+            nv[q] = fmaf(-v[i], w0, fmaf(-wi, v0, A[(k + 1 + i) * ld + (k + 1)]));
+            if (i >= 2) ss = fmaf(nv[q], nv[q], ss);
+          }
         }
-        __syncwarp();
-        if (k + 3 < K) householder(k + 1, vn);
+        if (k + 3 < K) {
+          ss = warp_sum_f(ss);
+          const float x0 = __shfl_sync(0xffffffffu, nv[0], 1);  // local row 1
+          float t = 0.f, beta = x0, scal = 0.f;
+          if (ss > 0.f) {
+            beta = -copysignf(sqrtf(x0 * x0 + ss), x0);
+            t = __fdividef(beta - x0, beta);
+            scal = __frcp_rn(x0 - beta);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i == 0) {
+              A[(k + 1) * ld + (k + 1)] = nv[q];
+            } else if (i < m) {
+              const float vv = (i == 1) ? 1.f : nv[q] * scal;
+              vn[i - 1] = vv;
+              A[(k + 1 + i) * ld + (k + 1)] = vv;
+            }
+          }
+          if (lane == 0) {
+            tau[k + 1] = t;
+            te[k + 1] = beta;
+            td[k + 1] = nv[0];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = lane + 32 * q;
+            if (i < m) A[(k + 1 + i) * ld + (k + 1)] = nv[q];
+          }
+        }
       } else {
         // the next trailing block (local rows and columns 1..m-1); local row 0
         // (the upper part of row k+1) is never read again
@@ -1349,6 +1390,7 @@ static size_t sym_eig_smem(int Kp) {
 
 void init_lanczos_attributes() {
   init_orth_attributes();
+
   cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_eig_smem(kMaxK));
   cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
 }
@@ -1379,8 +1421,8 @@ namespace psdp {
 // distributed shared memory: CTA c adds slice c of the entries over the C
 // partials in CTA order (deterministic), then every CTA gathers the full
 // matrix, so every CTA takes the same decisions.  The Cholesky factor of the
-// unit-diagonal Gram matrix is computed in FP32 by one warp (Crout order:
-// row j of R from the rows above it); a pivot below kOrthDefTol marks its
+// unit-diagonal Gram matrix is computed in FP32 by one warp with the matrix in
+// registers; a pivot below kOrthDefTol marks its
 // column as dependent, and that column is replaced by pseudo-random entries
 // which the next pass orthogonalises.
 constexpr float kOrthDefTol = 1e-5f;
@@ -1426,6 +1468,53 @@ __device__ __forceinline__ T cluster_sum(cooperative_groups::cluster_group& cl, 
 #pragma unroll
   for (int c = 0; c < 16; ++c) s += v[c];
   return s;
+}
+
+// One elimination step J of the warp Cholesky below (a template so that every
+// register index is a compile-time constant: the matrix never leaves registers).
+template <int W, int NC, int J>
+__device__ __forceinline__ void chol_warp_step(float (&g)[NC][W], float* R, float* rd, int* fl,
+                                               const double* d0s, int lane) {
+  if constexpr (J < W) {
+    const float piv = __shfl_sync(0xffffffffu, g[J / 32][J], J % 32);
+    const bool def = !(piv > kOrthDefTol);
+    const float inv = def ? 0.f : rsqrtf(piv);
+    float rj[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int l = lane + 32 * c;
+      rj[c] = (l > J) ? g[c][J] * inv : 0.f;
+      if (l < W) R[J * W + l] = (l == J) ? (def ? 1.f : piv * inv) : rj[c];
+    }
+    if (lane == 0) {
+      rd[J] = def ? 1.f : inv;
+      fl[J] = (def || d0s[J] <= 0.0) ? 1 : 0;
+    }
+#pragma unroll
+    for (int k = J + 1; k < W; ++k) {
+      const float rjk = __shfl_sync(0xffffffffu, rj[k / 32], k % 32);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) g[c][k] = fmaf(-rjk, rj[c], g[c][k]);
+    }
+    chol_warp_step<W, NC, J + 1>(g, R, rd, fl, d0s, lane);
+  }
+}
+
+// Cholesky of the unit-diagonal W x W matrix in G (upper triangle read) by one
+// warp, lane l holding columns l and l + 32 in registers; R (upper, row-major)
+// overwrites G, 1/R_jj goes to rd, dependency flags to fl.
+template <int W>
+__device__ __forceinline__ void chol_warp(float* G, float* rd, int* fl, const double* d0s, int lane) {
+  constexpr int NC = (W + 31) / 32;
+  float g[NC][W];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int l = lane + 32 * c;
+#pragma unroll
+    for (int k = 0; k < W; ++k) g[c][k] = (l < W && k <= l) ? G[k * W + l] : 0.f;
+  }
+  __syncwarp();
+  chol_warp_step<W, NC, 0>(g, G, rd, fl, d0s, lane);
 }
 
 template <int W>
@@ -1618,19 +1707,19 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
       __syncthreads();
       float dev = 0.f;
       for (int o0 = tid; o0 < ww; o0 += 4 * 256) {
-        double v[4];
+        float v[4];  // the reduced entries are FP64; the scaled Gram is FP32 (FP64 is 1/64 rate here)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int o = o0 + 256 * u;
-          v[u] = (o < ww && (o / W) <= (o % W)) ? cluster.map_shared_rank(PartG, o / chunk)[o] : 0.0;
+          v[u] = (o < ww && (o / W) <= (o % W)) ? (float)cluster.map_shared_rank(PartG, o / chunk)[o] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int o = o0 + 256 * u;
           if (o < ww) {
             const int a = o / W, b = o % W;
-            Gh[o] = (a <= b) ? (float)(v[u] * (double)sc[a] * (double)sc[b]) : 0.f;
-            if (a <= b) dev = fmaxf(dev, (float)fabs(v[u] - (a == b ? 1.0 : 0.0)));
+            Gh[o] = (a <= b) ? v[u] * sc[a] * sc[b] : 0.f;
+            if (a <= b) dev = fmaxf(dev, fabsf(v[u] - (a == b ? 1.f : 0.f)));
           }
         }
       }
@@ -1670,44 +1759,9 @@ __global__ void __launch_bounds__(256, 1) k_orth_cluster(float* __restrict__ Q, 
           for (int u = 0; u < 4; ++u) Zs[(4 * m + u) * ldr + i] = y[4 * m + u];
       }
     } else {
-      // ---- Cholesky of the unit-diagonal Gram matrix by warp 0 (Crout order,
-      // R in place of Gh's upper triangle, row j from rows 0..j-1)
-      if (tid < 32) {
-        const int lane = tid;
-        for (int j = 0; j < W; ++j) {
-          float sv[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int l = j + lane + 32 * h;
-            float sa[4] = {0.f, 0.f, 0.f, 0.f};
-            if (l < W) {
-              sa[0] = Gh[j * W + l];
-              int i = 0;
-#pragma unroll 2
-              for (; i + 3 < j; i += 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) sa[u] = fmaf(-Gh[(i + u) * W + j], Gh[(i + u) * W + l], sa[u]);
-              }
-              for (; i < j; ++i) sa[0] = fmaf(-Gh[i * W + j], Gh[i * W + l], sa[0]);
-            }
-            sv[h] = (sa[0] + sa[1]) + (sa[2] + sa[3]);
-          }
-          const float piv = __shfl_sync(0xffffffffu, sv[0], 0);
-          const bool def = !(piv > kOrthDefTol);
-          const float inv = def ? 0.f : rsqrtf(piv);
-          __syncwarp();  // every lane has read the entries of row j it needs
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int l = j + lane + 32 * h;
-            if (l < W) Gh[j * W + l] = (l == j) ? (def ? 1.f : piv * inv) : sv[h] * inv;
-          }
-          if (lane == 0) {
-            rd[j] = def ? 1.f : inv;
-            fl[j] = (def || d0s[j] <= 0.0) ? 1 : 0;
-          }
-          __syncwarp();
-        }
-      }
+      // ---- Cholesky of the unit-diagonal Gram matrix by warp 0, the matrix
+      // in registers (R written over Gh's upper triangle)
+      if (tid < 32) chol_warp<W>(Gh, rd, fl, d0s, tid);
       __syncthreads();
       // ---- Z <- Z D^{-1/2} R^{-1} by forward substitution, one row per thread
       // (x_j = (z_j - sum_{k<j} x_k R_kj) / R_jj; dependent columns get pseudo-random entries)
