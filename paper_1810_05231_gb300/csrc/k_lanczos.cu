@@ -222,12 +222,14 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
 
 // Inner-dimension slices per 128-row block: a power of two <= 8 (the cluster
 // size), about two CTAs per SM, at least four 32-wide chunks per slice.
+static int g_mv_cluster_max = 8;  // 16 where the device co-schedules 16-CTA clusters of this kernel
+
+// Slices of the inner dimension (= cluster size): split until about two CTAs
+// per SM, keeping at least two 32-column chunks per slice.
 static int matvec_slices(int n, int k) {
   const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
   int ns = 1;
-  while (ns < 8 && tiles * ns * 2 <= 2 * 148 && (n + 2 * ns * 4 * MV_KC - 1) / (2 * ns * 4 * MV_KC) >= 1 &&
-         n >= 2 * ns * 4 * MV_KC)
-    ns *= 2;
+  while (ns < g_mv_cluster_max && tiles * (2 * ns) <= 304 && n >= (2 * ns) * 2 * MV_KC) ns *= 2;
   return ns;
 }
 
@@ -1390,7 +1392,25 @@ static size_t sym_eig_smem(int Kp) {
 
 void init_lanczos_attributes() {
   init_orth_attributes();
-
+  {
+    cudaFuncSetAttribute(k_block_matvec<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_block_matvec<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_block_matvec<3>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(k_block_matvec<4>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    g_mv_cluster_max = (cudaOccupancyMaxActiveClusters(&nc, k_block_matvec<4>, &cfg) == cudaSuccess && nc > 0) ? 16 : 8;
+    cudaGetLastError();
+  }
   cudaFuncSetAttribute(k_sym_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_eig_smem(kMaxK));
   cudaFuncSetAttribute(k_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCholSmem);
 }
