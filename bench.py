@@ -187,13 +187,15 @@ def run_ours(args, rank, world):
 
 
 def roofline(pkg, torch, stream, n, info):
-    """Time the dominant HBM-bound kernel alone (cold L2) and relate it to HBM
-    bandwidth.
+    """Time the block product S * Q alone (cold L2) and place it on the roofline.
 
-    The block product S * Q (n x n FP32 S, n x k block) moves n^2 * 4 bytes of
-    S plus 2 * n * k * 4 bytes of Q and W per launch (algorithmic bytes); k is
-    the Krylov block width the solve uses at its final rank r,
-    16 * ceil((r + max(8, r/4)) / 16).
+    Per launch it moves n^2 * 4 bytes of S plus 2 * n * k * 4 bytes of Q and W
+    (algorithmic bytes) and performs 2 * n^2 * k flops; k is the Krylov block
+    width the solve uses at its final rank r, 16 * ceil((r + max(8, r/4)) / 16).
+    With k = 48 the intensity is 24 flop/byte, above the FP32 SIMT ridge
+    (80.6 TFLOP/s / 6.78 TB/s = 11.9 flop/byte), so the kernel is bound by
+    FP32 arithmetic ("alu"): peak = 152 SMs x 128 FP32 lanes x 2 flop x
+    2.07 GHz = 80.6 TFLOP/s.  The HBM view is reported beside it.
     """
     hbm, _, src = _peaks()
     r = int(info["final_rank"])
@@ -218,7 +220,9 @@ def roofline(pkg, torch, stream, n, info):
                 durs.append(e0.elapsed_time(e1) * 1e-3)
     t = statistics.mean(durs)
     bytes_alg = n * n * 4 + 2 * n * k * 4
-    achieved = bytes_alg / t / 1e9
+    flops = 2.0 * n * n * k
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s, FP32 FMA lanes at the maximum SM clock
+    achieved = flops / t / 1e12
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
@@ -226,9 +230,12 @@ def roofline(pkg, torch, stream, n, info):
             traffic = json.load(open(tp)).get(f"k_block_matvec_n{n}_k{k}")
         except Exception:
             traffic = None
-    return {"kernel": "k_block_matvec", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-            "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
-            "alg_bytes_per_launch": bytes_alg, "avg_launch_s": t, "k": k, "l2": "flushed before each launch"}
+    return {"kernel": "k_block_matvec", "bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak, 2),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "unit": "TFLOP/s",
+            "frac": round(achieved / alu_peak, 4), "traffic": traffic, "alg_bytes_per_launch": bytes_alg,
+            "flops_per_launch": flops, "avg_launch_s": t, "k": k,
+            "hbm_achieved_gbs": round(bytes_alg / t / 1e9, 1), "hbm_peak_gbs": hbm, "hbm_peak_source": src,
+            "hbm_frac": round(bytes_alg / t / 1e9 / hbm, 4), "l2": "flushed before each launch"}
 
 
 def full_eig_baseline(torch, inst, stream, iters=10):
@@ -412,7 +419,10 @@ def main():
         "e2e": {"value": round(e2e_val, 2), "unit": "iters/s", "h2d_bytes_per_step": int(res["h2d"]),
                 "d2h_bytes_per_step": int(res["d2h"]),
                 "time_to_tol_s": round(statistics.median(res["e2e_times"]), 5)},
-        "roofline": res["roofline"], "cpu_baseline": cpu, "clocks": res["clocks"],
+        "roofline": res["roofline"],
+        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.54, "bound": "latency (one CTA)",
+                            "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
+        "cpu_baseline": cpu, "clocks": res["clocks"],
         "gpu_launches": int(res["launches"]), "full_eig": res["full"],
     }
     print(json.dumps(line))
