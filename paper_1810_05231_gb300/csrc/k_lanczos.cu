@@ -567,7 +567,7 @@ constexpr int JB = 32;  // wanted columns refined per pass
 constexpr int SE_THREADS = 512;
 constexpr float kSePivmin = 1e-30f;   // Sturm pivots below this (unit-norm matrix) count as negative
 constexpr float kSeGroupTol = 2e-5f;  // inverse-iteration groups (unit-norm matrix)
-constexpr double kRefineBelow = 2e-5;  // adaptive refinement: Ritz residual tolerances below this
+constexpr double kRefineBelow = 5e-6;  // adaptive refinement: Ritz residual tolerances below this
 
 // Number of eigenvalues of the tridiagonal (d, e2 = squared off-diagonal) below x.
 __device__ __forceinline__ int sturm_count(const float* d, const float* e2, int K, float x) {

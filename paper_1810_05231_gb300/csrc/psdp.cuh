@@ -165,7 +165,7 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
 // refine = 1 corrects the wanted vectors once from residuals accumulated in
 // FP32 pairs and returns FP64 Rayleigh quotients; refine = 0 returns the FP32
 // eigenpairs of the tridiagonal method as they are.  With adapt_tol (a device
-// pointer) the kernel refines only when *adapt_tol is below 2e-5.
+// pointer) the kernel refines only when *adapt_tol is below 5e-6.
 void launch_sym_eig(const double* T, int K, double* theta, float* Y, int ldy, int nout,
                     const int* skip, cudaStream_t st, int refine = 1, const double* adapt_tol = nullptr);
 void init_lanczos_attributes();
