@@ -681,13 +681,15 @@ __device__ void tri_lu_slot(const float* d, const float* e, int K, float lam, fl
     float l;
     if (fabsf(p0) >= fabsf(s0)) {
       if (p0 == 0.f) p0 = tiny;
-      l = s0 / p0;
-      rp[i * ns + s] = 1.f / p0;
+      const float rcp = __frcp_rn(p0);  // one reciprocal per step, shared by l and the pivot
+      l = s0 * rcp;
+      rp[i * ns + s] = rcp;
       p0 = s1 - l * p1;
       p1 = s2;
     } else {
-      l = p0 / s0;
-      rp[i * ns + s] = 1.f / s0;
+      const float rcp = __frcp_rn(s0);
+      l = p0 * rcp;
+      rp[i * ns + s] = rcp;
       bits |= 1u << (i & 31);
       p0 = p1 - l * s1;
       p1 = -l * s2;
@@ -698,7 +700,7 @@ __device__ void tri_lu_slot(const float* d, const float* e, int K, float lam, fl
       bits = 0u;
     }
   }
-  rp[(K - 1) * ns + s] = 1.f / ((p0 == 0.f) ? tiny : p0);
+  rp[(K - 1) * ns + s] = __frcp_rn((p0 == 0.f) ? tiny : p0);
 }
 
 __device__ void tri_solve_slot(const float* d, const float* e, int K, float lam, const float* lm, const float* rp,
@@ -1140,8 +1142,18 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
   __syncthreads();
 
   // ---- (4) back-transformation V <- H_0 ... H_{K-3} V: each warp applies all
-  // reflectors (last first) to its own columns, four at a time
+  // reflectors (last first) to its own columns, four at a time, two
+  // reflectors per reduction round: with a = v_b^T y, b = v_a^T y and
+  // c = v_a^T v_b, H_a H_b y = y - tau_b a v_b - tau_a (b - tau_b a c) v_a
   {
+    float* pc = pb;  // c for the pair (k - 1, k), at index k - 1
+    for (int k0 = warp; k0 + 1 <= K - 3; k0 += nwarps) {
+      float c = 0.f;
+      for (int i = k0 + 2 + lane; i < K; i += 32) c = fmaf(A[i * ld + k0], A[i * ld + k0 + 1], c);
+      c = warp_sum_f(c);
+      if (lane == 0) pc[k0] = c;
+    }
+    __syncthreads();
     const int ncols = K - a_need;
     for (int c0 = warp; c0 < ncols; c0 += 4 * nwarps) {
       int col[4];
@@ -1152,23 +1164,36 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         use[u] = j < ncols;
         col[u] = use[u] ? a_need + j : a_need + c0;
       }
-      for (int k = K - 3; k >= 0; --k) {
-        const float tk = tau[k];
-        if (tk == 0.f) continue;
-        const int m = K - k - 1;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int i = lane; i < m; i += 32) {
-          const float vi = A[(k + 1 + i) * ld + k];
+      for (int k = K - 3; k >= 0; k -= 2) {
+        const int kb = k, ka = k - 1;  // H_kb first, then H_ka
+        const float tb = tau[kb], ta = (ka >= 0) ? tau[ka] : 0.f;
+        if (tb == 0.f && ta == 0.f) continue;
+        const int i0 = (ka >= 0) ? ka + 1 : kb + 1;
+        float av[4] = {0.f, 0.f, 0.f, 0.f}, bv[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = i0 + lane; i < K; i += 32) {
+          const float v1 = (i >= kb + 1) ? A[i * ld + kb] : 0.f;
+          const float v0 = (ka >= 0) ? A[i * ld + ka] : 0.f;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = fmaf(vi, V[(k + 1 + i) * ld + col[u]], acc[u]);
+          for (int u = 0; u < 4; ++u) {
+            const float yv = V[i * ld + col[u]];
+            av[u] = fmaf(v1, yv, av[u]);
+            bv[u] = fmaf(v0, yv, bv[u]);
+          }
         }
+        const float cc = (ka >= 0) ? pc[ka] : 0.f;
+        float s1[4], s0[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = tk * warp_sum_f(acc[u]);
-        for (int i = lane; i < m; i += 32) {
-          const float vi = A[(k + 1 + i) * ld + k];
+        for (int u = 0; u < 4; ++u) {
+          const float a = warp_sum_f(av[u]), bb = warp_sum_f(bv[u]);
+          s1[u] = tb * a;
+          s0[u] = ta * (bb - tb * a * cc);
+        }
+        for (int i = i0 + lane; i < K; i += 32) {
+          const float v1 = (i >= kb + 1) ? A[i * ld + kb] : 0.f;
+          const float v0 = (ka >= 0) ? A[i * ld + ka] : 0.f;
 #pragma unroll
           for (int u = 0; u < 4; ++u)
-            if (use[u]) V[(k + 1 + i) * ld + col[u]] = fmaf(-vi, acc[u], V[(k + 1 + i) * ld + col[u]]);
+            if (use[u]) V[i * ld + col[u]] = fmaf(-s1[u], v1, fmaf(-s0[u], v0, V[i * ld + col[u]]));
         }
         __syncwarp();
       }
