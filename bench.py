@@ -110,8 +110,12 @@ def workload_problem():
     return si.config_maxcut_2000()
 
 
-def settings_for(pkg, **kw):
-    s = pkg.default_settings(tol=1e-4, rank_init=8, block_size=16, check_every=50)
+OPERATOR_FORMS = {"explicit": 0, "factored": 1, "auto": 2}  # settings.operator_form
+
+
+def settings_for(pkg, operator="explicit", **kw):
+    s = pkg.default_settings(tol=1e-4, rank_init=8, block_size=16, check_every=50,
+                             operator_form=OPERATOR_FORMS[operator])
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -133,7 +137,7 @@ def run_ours(args, rank, world):
     n = inst.n
     flush = torch.zeros(128 * 1024 * 1024, dtype=torch.float32, device=dev)
     with torch.cuda.stream(stream):
-        slv = pkg.Solver(settings_for(pkg), stream=stream.cuda_stream)
+        slv = pkg.Solver(settings_for(pkg, args.operator), stream=stream.cuda_stream)
         slv.set_instance(inst)
         for _ in range(args.warmup):
             slv.solve()
@@ -166,7 +170,7 @@ def run_ours(args, rank, world):
            inst.C_idx.nbytes + inst.C_val.nbytes)
     d2h = 0
     with torch.cuda.stream(stream):
-        slv2 = pkg.Solver(settings_for(pkg), stream=stream.cuda_stream)
+        slv2 = pkg.Solver(settings_for(pkg, args.operator), stream=stream.cuda_stream)
         for _ in range(max(1, args.steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -180,10 +184,40 @@ def run_ours(args, rank, world):
         slv2.close()
     roof = roofline(pkg, torch, stream, n, infos[-1])
     full = full_eig_baseline(torch, inst, stream, iters=args.full_eig_iters) if args.full_eig_iters > 0 else None
+    other = args.other_operator
+    alt = (operator_form_run(pkg, torch, stream, inst, flush, other, args.steps, min(args.warmup, 2))
+           if other != "none" and other != args.operator else None)
     res = dict(times=times, iters=iters, infos=infos, clocks=clk, e2e_times=e2e_times, e2e_iters=e2e_iters,
-               h2d=h2d, d2h=d2h, roofline=roof, full=full, launches=sum(i["kernel_launches"] for i in infos))
+               h2d=h2d, d2h=d2h, roofline=roof, full=full, launches=sum(i["kernel_launches"] for i in infos),
+               alt=alt)
     slv.close()
     return res
+
+
+def operator_form_run(pkg, torch, stream, inst, flush, operator, steps, warmup):
+    """The same timed solves with the other operator form of S^k (the factored
+    one applies S^k from the factors of X^k and never writes it to HBM)."""
+    with torch.cuda.stream(stream):
+        slv = pkg.Solver(settings_for(pkg, operator), stream=stream.cuda_stream)
+        slv.set_instance(inst)
+        for _ in range(warmup):
+            slv.solve()
+        times, iters, launches = [], [], 0
+        for _ in range(steps):
+            flush_l2(torch, flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = slv.solve()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+            iters.append(info.iters)
+            launches += info.kernel_launches
+        slv.close()
+    return {"operator": operator, "value": round(sum(iters) / sum(times), 2), "unit": "iters/s",
+            "time_to_tol_s": round(statistics.median(times), 5), "iters_per_solve": int(statistics.median(iters)),
+            "final_rank": info.final_rank, "rel_gap": info.rel_gap, "gpu_launches": int(launches)}
 
 
 def roofline(pkg, torch, stream, n, info):
@@ -343,6 +377,10 @@ def main():
     ap.add_argument("--full-eig-iters", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"])
+    ap.add_argument("--operator", default="explicit", choices=sorted(OPERATOR_FORMS),
+                    help="how the projection applies S^k: formed in HBM, or from the factors of X^k")
+    ap.add_argument("--other-operator", default="factored", choices=sorted(OPERATOR_FORMS) + ["none"],
+                    help="also time the solves with this operator form (reported beside the line)")
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--host-threads", type=int, default=48)
     args = ap.parse_args()
@@ -409,7 +447,7 @@ def main():
         "metric": METRIC, "value": round(value, 2), "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * total_t / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 2000, "rank_init": 8, "block": 16, "tol": 1e-4,
+        "config": {"workload": WORKLOAD, "n": 2000, "rank_init": 8, "block": 16, "tol": 1e-4, "operator": args.operator,
                    "l2": "flushed before each timed solve", "parallelism": "replicas" if world > 1 else "single"},
         "time_to_tol_s": round(statistics.median(res["times"]), 5),
         "iters_per_solve": int(statistics.median(res["iters"])),
@@ -423,7 +461,7 @@ def main():
         "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.54, "bound": "latency (one CTA)",
                             "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
         "cpu_baseline": cpu, "clocks": res["clocks"],
-        "gpu_launches": int(res["launches"]), "full_eig": res["full"],
+        "gpu_launches": int(res["launches"]), "full_eig": res["full"], "other_operator_form": res["alt"],
     }
     print(json.dumps(line))
     if world > 1:

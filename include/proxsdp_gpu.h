@@ -72,6 +72,18 @@ extern "C" {
 /* precision of the S * V products and the rebuild */
 #define PROXSDP_PREC_FP32 0
 
+/* proxsdp_gpu_settings.operator_form: how the projection applies
+ * S^k = X^k - alpha (C + M*(y^k)) (Alg. 2 primal step) to its Krylov blocks.
+ * EXPLICIT writes S^k (n*n FP32) to device memory every iteration and
+ * multiplies it; FACTORED never forms it and applies
+ * V Lambda_+ V^T Q - alpha (C + M*(y^k)) Q from the factors of X^k (Sec. 3)
+ * and the union sparsity pattern of C and the A_i, O(n r w + nnz w) per
+ * product; AUTO takes FACTORED when that pattern holds at most n*n/8 entries.
+ * Problems with n <= 128 and Alg. 1 (full_eig) always use the explicit S. */
+#define PROXSDP_OP_EXPLICIT 0
+#define PROXSDP_OP_FACTORED 1
+#define PROXSDP_OP_AUTO 2
+
 typedef struct proxsdp_gpu_ctx* proxsdp_gpu_t;
 
 /* Settings; proxsdp_gpu_settings_default fills the defaults listed here. */
@@ -95,6 +107,7 @@ typedef struct {
   int guard;              /* extra Ritz vectors kept beyond r (0: automatic)             [0]   */
   int check_every;        /* iterations between host checks of the stop status           [50]  */
   int use_graphs;         /* run the iteration as a CUDA graph with conditional nodes    [1]   */
+  int operator_form;      /* PROXSDP_OP_EXPLICIT / _FACTORED / _AUTO                     [0]   */
 } proxsdp_gpu_settings;
 
 typedef struct {

@@ -8,6 +8,9 @@ from ._binding import (  # noqa: F401
     CONVERGED,
     MAX_ITER,
     NUMERIC_ERROR,
+    OP_AUTO,
+    OP_EXPLICIT,
+    OP_FACTORED,
     STALLED_AT_MAX_RANK,
     TIME_LIMIT,
     EXPORTED,

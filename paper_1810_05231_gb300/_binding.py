@@ -29,6 +29,10 @@ TIME_LIMIT = 2
 STALLED_AT_MAX_RANK = 3
 NUMERIC_ERROR = 4
 
+OP_EXPLICIT = 0  # settings.operator_form: S^k written to device memory and multiplied
+OP_FACTORED = 1  # S^k applied from the factors of X^k and the sparse C + M*(y^k)
+OP_AUTO = 2      # factored when the union pattern holds at most n*n/8 entries
+
 EXPORTED = [
     "proxsdp_gpu_settings_default",
     "proxsdp_gpu_create",
@@ -69,6 +73,7 @@ class Settings(ctypes.Structure):
         ("guard", ctypes.c_int),
         ("check_every", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
+        ("operator_form", ctypes.c_int),
     ]
 
 

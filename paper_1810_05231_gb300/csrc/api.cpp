@@ -279,6 +279,30 @@ int preprocess(const proxsdp_gpu_settings& set, int64_t n64, const double* C_den
       h.tile_u[fill[t]++] = u;
     }
   }
+  // rows of the full pattern (the factored operator's sparse part; left empty
+  // when the pattern has more entries than an int indexes)
+  if (2 * (int64_t)nU < (int64_t)INT32_MAX) {
+    h.sym_ptr.assign((size_t)n + 1, 0);
+    for (int u = 0; u < nU; ++u) {
+      h.sym_ptr[(size_t)h.u_p[u] + 1] += 1;
+      if (h.u_p[u] != h.u_q[u]) h.sym_ptr[(size_t)h.u_q[u] + 1] += 1;
+    }
+    for (int i = 0; i < n; ++i) h.sym_ptr[(size_t)i + 1] += h.sym_ptr[i];
+    h.sym_col.resize(h.sym_ptr[n]);
+    h.u_pos.assign(2 * (size_t)nU, -1);
+    {
+      std::vector<int> at(h.sym_ptr.begin(), h.sym_ptr.end() - 1);
+      for (int u = 0; u < nU; ++u) {
+        const int p = h.u_p[u], q = h.u_q[u];
+        h.u_pos[2 * (size_t)u] = at[p];
+        h.sym_col[at[p]++] = q;
+        if (p != q) {
+          h.u_pos[2 * (size_t)u + 1] = at[q];
+          h.sym_col[at[q]++] = p;
+        }
+      }
+    }
+  }
   // norms for the relative residuals
   double c2 = 0.0;
   for (int u = 0; u < nU; ++u) c2 += (h.u_p[u] == h.u_q[u] ? 1.0 : 2.0) * h.u_c[u] * h.u_c[u];
@@ -339,7 +363,8 @@ int check_settings(const proxsdp_gpu_settings& s, std::string& err) {
   if (!(s.tol > 0.0) || s.max_iter < 0 || s.rank_init < 1 || s.block_size < 1 || s.window < 1 ||
       s.window > psdp::kMaxWindow || !(s.alpha_frac > 0.0 && s.alpha_frac < 1.0) || s.max_rank < 1 ||
       s.lanczos_max_cycles < 1 || s.lanczos_steps < 0 || s.lanczos_tol < 0.0 || s.guard < 0 ||
-      s.check_every < 1 || s.precision != PROXSDP_PREC_FP32) {
+      s.check_every < 1 || s.precision != PROXSDP_PREC_FP32 || s.operator_form < PROXSDP_OP_EXPLICIT ||
+      s.operator_form > PROXSDP_OP_AUTO) {
     err = "invalid settings";
     return PROXSDP_ERR_INVALID_ARG;
   }
@@ -402,6 +427,7 @@ int proxsdp_gpu_settings_default(proxsdp_gpu_settings* s) {
   s->guard = 0;
   s->check_every = 50;
   s->use_graphs = 1;
+  s->operator_form = PROXSDP_OP_EXPLICIT;
   return PROXSDP_OK;
 }
 

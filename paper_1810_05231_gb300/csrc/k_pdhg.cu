@@ -357,6 +357,12 @@ __global__ void __launch_bounds__(256) k_dvals(DevProblem pb, DevWork wk) {
       md += wk.dy[pb.u_row[j]] * pb.u_a[j];
     }
     wk.D[u] = d;
+    if (wk.Dsym) {  // factored operator: alpha D on both triangles, as the rebuild subtracts it
+      const float ad = (float)(pb.alpha * d);
+      wk.Dsym[pb.u_pos[2 * (size_t)u]] = ad;
+      const int p2 = pb.u_pos[2 * (size_t)u + 1];
+      if (p2 >= 0) wk.Dsym[p2] = ad;
+    }
     const double wgt = (pb.u_p[u] == pb.u_q[u]) ? 1.0 : 2.0;
     v[0] = wgt * md * md;
     v[1] = wgt * md;

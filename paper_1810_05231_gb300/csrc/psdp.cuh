@@ -100,6 +100,14 @@ struct DevProblem {
   double alpha;
   double normC, normRhs;       // ||C||_F, ||rhs||_2 (scaled problem)
   const double* C_dense;       // dense C (row-major n x n) or nullptr
+  // rows of the full (both triangles) union pattern, for the factored
+  // operator: row i holds entries [sym_ptr[i], sym_ptr[i+1]) at columns
+  // sym_col; union entry u sits at u_pos[2u] (row u_p) and, off the diagonal,
+  // at u_pos[2u+1] (row u_q; -1 on the diagonal)
+  int nsym;
+  const int* sym_ptr;          // n + 1
+  const int* sym_col;
+  const int* u_pos;            // 2 nU
 };
 
 // Work buffers.
@@ -126,6 +134,10 @@ struct DevWork {
   double* Hx;                  // Gram of the factor slots (2 kMaxR)^2
   float* mv_part;              // split-K partials of the block product
   unsigned* mv_cnt;            // its per-tile counters
+  // factored operator (S never formed; all three nullptr on the explicit path)
+  float* Dsym;                 // (float)(alpha * D) on the full pattern, CSR order of sym_col
+  float* Qr;                   // row-major copy of the block being multiplied (n x w)
+  float* lrP;                  // its coefficient block [Lambda_+ V^T Q ; -alpha s0 1^T Q]
   Ctl* ctl;
 };
 
@@ -187,6 +199,19 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int i
                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 // sel = 0: factors of the current iterate (Ctl::par); sel = 1: the other buffer.
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// launchers (k_factored.cu)
+// ---------------------------------------------------------------------------
+// W = S^k Q for the w <= 64 columns of Q without S: S^k = V Lambda_+ V^T -
+// alpha (D_sym + s0 11^T) with the factors of the current iterate (Ctl::par,
+// Ctl::r_old columns) and Dsym / dshift[0] as written by the last launch_dvals.
+// Two kernels; the second sets the graph conditional `cond` to 1 when set_cond.
+void launch_factored_matvec(const DevProblem& pb, const DevWork& wk, const float* Q, int ldq, float* W,
+                            int ldw, int w, const int* skip, cudaStream_t st,
+                            cudaGraphConditionalHandle cond = 0, int set_cond = 0);
+constexpr int kFactoredLaunches = 2;  // kernels per factored product
+void init_factored_attributes();
 void launch_copy_cols(const float* src, int lds, float* dst, int ldd, int n, int k, const int* skip,
                       cudaStream_t st);
 void launch_full_eig_factors(const DevWork& wk, int n, cudaStream_t st);

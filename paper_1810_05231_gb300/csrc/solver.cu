@@ -85,6 +85,7 @@ void init_kernel_attributes() {
   if (dev < 0 || dev >= 256 || done[dev]) return;
   init_pdhg_attributes();
   init_lanczos_attributes();
+  init_factored_attributes();
   done[dev] = true;
 }
 
@@ -178,6 +179,20 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   P.normC = h.normC;
   P.normRhs = h.normRhs;
   P.C_dense = nullptr;
+  // operator form of S^k: the factored one needs the Lanczos path and the
+  // row structure of the union pattern
+  const bool lanczos_path = !(n <= kFullEigMax || set.full_eig);
+  const int64_t nsym = (int64_t)h.sym_col.size();
+  factored = lanczos_path && !h.sym_ptr.empty() &&
+             (set.operator_form == PROXSDP_OP_FACTORED ||
+              (set.operator_form == PROXSDP_OP_AUTO && 8 * nsym <= (int64_t)n * n));
+  if (factored) {
+    alloc_S = false;
+    P.nsym = (int)nsym;
+    CKA(dupload(allocs, &P.sym_ptr, h.sym_ptr, st));
+    CKA(dupload(allocs, &P.sym_col, h.sym_col, st));
+    CKA(dupload(allocs, &P.u_pos, h.u_pos, st));
+  }
 
   DevWork& Wk = wk;
   Wk = DevWork{};
@@ -212,6 +227,12 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   CKA(dalloc(allocs, &Hx, (size_t)4 * kMaxR * kMaxR));
   Wk.Vcm = Vcm;
   Wk.Hx = Hx;
+  if (factored) {
+    CKA(dalloc(allocs, &Wk.Dsym, (size_t)nsym));
+    CKA(dalloc(allocs, &Wk.Qr, (size_t)n * kMaxW));
+    CKA(dalloc(allocs, &Wk.lrP, (size_t)64 * kMaxW));
+    CK(cudaMemsetAsync(Wk.Dsym, 0, sizeof(float) * std::max<size_t>((size_t)nsym, 1), st));
+  }
   CKA(dalloc(allocs, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxW)));
   CKA(dalloc(allocs, &Wk.mv_cnt, block_matvec_counters(n, kMaxW)));
   CK(cudaMemsetAsync(Wk.mv_cnt, 0, sizeof(unsigned) * block_matvec_counters(n, kMaxW), st));
@@ -295,19 +316,21 @@ static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned lon
 
 void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
                    unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
-                   cudaStream_t st) {
+                   cudaStream_t st, const DevProblem* fac) {
   const int* skip = &wk.ctl->lz_done;
   for (int j = 1; j <= s; ++j) {
     enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st, wk.W + (size_t)(j - 1) * w * wk.ldq);
-    launch_block_matvec(wk.S, wk.lds, n, wk.Q + (size_t)j * w * wk.ldq, wk.ldq,
-                        wk.W + (size_t)j * w * wk.ldq, wk.ldq, w, skip, st, wk.mv_part, wk.mv_cnt);
+    const float* Qj = wk.Q + (size_t)j * w * wk.ldq;
+    float* Wj = wk.W + (size_t)j * w * wk.ldq;
+    if (fac) launch_factored_matvec(*fac, wk, Qj, wk.ldq, Wj, wk.ldq, w, skip, st);
+    else launch_block_matvec(wk.S, wk.lds, n, Qj, wk.ldq, Wj, wk.ldq, w, skip, st, wk.mv_part, wk.mv_cnt);
     dbg(wk, "cycle matvec", st);
   }
   launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
   dbg(wk, "rr gram T", st);
   launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
   dbg(wk, "rr eig", st);
-  int cycle_launches = 3 + s;  // Gram of T, eigensolver, Ritz; one product per step
+  int cycle_launches = 3 + s * (fac ? kFactoredLaunches : 1);  // Gram of T, eigensolver, Ritz; the products
   for (int j = 1; j <= s; ++j) cycle_launches += orth_cluster_applies(n, j * w, w) ? 1 : 11;
   launch_ritz(wk, n, K, w, r, s, cycle_launches, cond, use_cond, st);
   dbg(wk, "ritz", st);
@@ -325,8 +348,11 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   } else {
     if (g_debug) g_debug_n = n;
     enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
-    launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, wk.mv_part, wk.mv_cnt,
-                        inner, use);
+    if (factored)
+      launch_factored_matvec(pb, wk, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, inner, use);
+    else
+      launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, wk.mv_part, wk.mv_cnt,
+                          inner, use);
     dbg(wk, "warm matvec", st);
     if (in_graph) {
       cudaStreamCaptureStatus cs;
@@ -345,13 +371,13 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
       CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
       cudaGraph_t body = p.conditional.phGraph_out[0];
       CK(cudaStreamBeginCaptureToGraph(st_aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-      enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 1, st_aux);
+      enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 1, st_aux, factored ? &pb : nullptr);
       CK(cudaStreamEndCapture(st_aux, &body));
     } else {
       // direct launches: the same kernels as the graph body, with the host
       // reading the projection's convergence flag after every restart cycle
       for (int c = 0; c < std::max(1, set.lanczos_max_cycles); ++c) {
-        enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 0, st);
+        enqueue_cycle(wk, n, k.w, k.K, k.s, k.r, seed, inner, 0, st, factored ? &pb : nullptr);
         int done = 0;
         CK(cudaMemcpyAsync(&ctl_host->lz_done, &wk.ctl->lz_done, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -365,12 +391,17 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   launch_dvals(pb, wk, st);
   dbg(wk, "mxdual/dvals", st);
   const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
-  // kernels per iteration outside the restart cycles
-  const int iter_launches = k.full ? 7 : (orth_cluster_applies(n, 0, k.w) ? 1 : 3) + 5;
+  // kernels per iteration outside the restart cycles: Cholesky-QR, the warm
+  // product, M(X)/dual step, D values, Gram + controller, the rebuild of S
+  const int iter_launches = k.full ? 7
+                                   : (orth_cluster_applies(n, 0, k.w) ? 1 : 3) +
+                                         (factored ? kFactoredLaunches + 3 : 5);
   launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
   dbg(wk, "gram+control", st);
-  launch_rebuild(pb, wk, k.r, 0, st);
-  dbg(wk, "rebuild", st);
+  if (!factored) {
+    launch_rebuild(pb, wk, k.r, 0, st);
+    dbg(wk, "rebuild", st);
+  }
   CK(cudaGetLastError());
   return PROXSDP_OK;
 }
@@ -460,7 +491,7 @@ int Solver::init_iterate_zero() {
   CK(cudaMemcpyAsync(wk.ctl, ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   // D = C (y = 0), S^0 = -alpha C
   launch_dvals(pb, wk, st);
-  launch_rebuild(pb, wk, 1, 0, st);
+  if (!factored) launch_rebuild(pb, wk, 1, 0, st);
   if (!(n <= kFullEigMax || set.full_eig)) {
     launch_random_block(wk.Q, wk.ldq, n, 0, w, seed, st);
     enqueue_orth(wk, n, 0, w, seed, nullptr, st);
@@ -654,7 +685,7 @@ int Solver::set_iterate(int rr, const double* V, const double* lam, const double
   CK(cudaMemcpyAsync(wk.ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   // S^k = X^k - alpha (C + M*(y^k)), Lanczos warm start = the given factors
   launch_dvals(pb, wk, st);
-  launch_rebuild(pb, wk, rr, 0, st);
+  if (!factored) launch_rebuild(pb, wk, rr, 0, st);
   if (!(n <= kFullEigMax || set.full_eig)) {
     CK(cudaMemcpyAsync(wk.Q, vcm.data(), sizeof(float) * (size_t)wk.ldq * std::min(rr, w),
                        cudaMemcpyHostToDevice, st));

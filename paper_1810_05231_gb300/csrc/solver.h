@@ -28,6 +28,7 @@ struct HostProblem {
   std::vector<double> u_c, u_a;
   int ntile = 0;
   std::vector<int> tile_ptr, tile_loc, tile_u;
+  std::vector<int> sym_ptr, sym_col, u_pos;
   double normM = 1.0, alpha = 0.0, normC = 0.0, normRhs = 0.0;
 };
 
@@ -54,6 +55,7 @@ struct Solver {
   std::vector<void*> allocs;
   Ctl* ctl_host = nullptr;  // pinned mirror
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  bool factored = false;  // S^k applied from the factors (never formed)
   int r = 8;
   int rank_changes = 0;
   int k_target = 32;  // Rayleigh-Ritz basis size aimed at by dims() (one Krylov step per cycle)
@@ -88,7 +90,10 @@ void init_kernel_attributes();
 // and within itself; one restart cycle of the block Krylov projection.
 void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long seed, const int* skip,
                   cudaStream_t st, const float* src = nullptr);
+// With `fac` (the problem of a factored-operator solve) the block products
+// apply S^k from the factors instead of reading wk.S.
 void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r, unsigned long long seed,
-                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
+                   cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st,
+                   const DevProblem* fac = nullptr);
 
 }  // namespace psdp

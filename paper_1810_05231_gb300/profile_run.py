@@ -7,7 +7,8 @@ launch individually:
 The workload is the MaxCut SDP relaxation (Sec. 5.1) of the seeded weighted
 Erdos-Renyi graph G(2000, 0.01) with integer weights 1..5 (seed 1); ``--rank``
 sets the initial target rank r (the block width follows from it).  Prints the
-solver's info record as one line.
+solver's info record as one line.  ``--operator factored`` applies S^k from
+the factors of X^k instead of forming it.
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ def main(argv=None) -> int:
     ap.add_argument("--iters", type=int, default=150)
     ap.add_argument("--rank", type=int, default=32)
     ap.add_argument("--graphs", action="store_true", help="use the graph-captured loop instead")
+    ap.add_argument("--operator", choices=["explicit", "factored", "auto"], default="explicit")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import sdp_instances as si
@@ -29,8 +31,9 @@ def main(argv=None) -> int:
     import paper_1810_05231_gb300 as pkg
 
     inst = si.config_maxcut_2000()
+    form = {"explicit": pkg.OP_EXPLICIT, "factored": pkg.OP_FACTORED, "auto": pkg.OP_AUTO}[args.operator]
     slv = pkg.Solver(tol=1e-4, rank_init=args.rank, block_size=16, use_graphs=1 if args.graphs else 0,
-                     check_every=1000)
+                     check_every=1000, operator_form=form)
     slv.set_instance(inst)
     info = slv.iterate(args.iters)
     print(json.dumps(info.as_dict()))

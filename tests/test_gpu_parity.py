@@ -121,8 +121,11 @@ def _shared_iterate(inst, r, iters):
     return prob, U[:, ::-1][:, :r].copy(), lam_x[::-1][:r].copy(), res.y_paper
 
 
+@pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
 @pytest.mark.parametrize("kind,n,r", [("maxcut", 200, 4), ("maxcut", 90, 6), ("equi", 160, 8), ("sensor", 0, 8)])
-def test_one_iteration_matches_oracle(pkg, kind, n, r):
+def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
+    """form 1 applies S^k from the factors of X^k (n > 128; n = 90 takes the
+    dense eigensolver, which always forms S)."""
     if kind == "maxcut":
         inst = si.maxcut_er(n, 0.05, 3)
     elif kind == "equi":
@@ -133,7 +136,7 @@ def test_one_iteration_matches_oracle(pkg, kind, n, r):
         inst = si.sensor_network(140, 6, 0.3, seed=5)
     prob, Vx, lx, yp = _shared_iterate(inst, r, 25)
     sp, scale = normalize_rows(prob)
-    slv = pkg.Solver(rank_init=r, max_rank=r, lanczos_tol=1e-6, lanczos_max_cycles=30)
+    slv = pkg.Solver(rank_init=r, max_rank=r, lanczos_tol=1e-6, lanczos_max_cycles=30, operator_form=form)
     slv.set_instance(inst)
     slv.set_iterate(Vx, lx, yp)
     info = slv.iterate(1)
@@ -211,9 +214,11 @@ def test_maxcut_random_against_oracle(pkg, n, p, seed):
     slv.close()
 
 
-def test_equipartition_dense_row(pkg):
+@pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
+def test_equipartition_dense_row(pkg, form):
     """Equipartition (Sec. 5.1) with the structured row tr(11^T X) = 0, n > 128
-    (Lanczos path), against the oracle's LR-PD-SDP and its certificates."""
+    (Lanczos path), against the oracle's LR-PD-SDP and its certificates.  The
+    factored operator carries the 11^T term as a column of ones."""
     n = 140
     rng = np.random.default_rng(12)
     ei, ej = si.erdos_renyi(n, 0.06, rng)
@@ -223,7 +228,7 @@ def test_equipartition_dense_row(pkg):
     # residual and gap target, so each objective is within ~1e-4 of the optimum
     ref = oracle.solve(prob, mode="lr", tol=1e-4, rank_init=16, max_iter=20000)
     assert ref.status == 0  # converged
-    slv = pkg.Solver(tol=1e-4, rank_init=16, max_iter=100000)
+    slv = pkg.Solver(tol=1e-4, rank_init=16, max_iter=100000, operator_form=form)
     slv.set_instance(inst)
     info = slv.solve()
     assert info.status == pkg.CONVERGED, info.as_dict()
@@ -265,9 +270,10 @@ def test_inequality_rows(pkg):
 # the n = 2000 MaxCut workload (weights 1..5), certified at full size
 # ---------------------------------------------------------------------------
 
-def test_maxcut_2000_certified(pkg):
+@pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
+def test_maxcut_2000_certified(pkg, form):
     inst = si.config_maxcut_2000()
-    slv = pkg.Solver(tol=1e-4, rank_init=8, block_size=16)
+    slv = pkg.Solver(tol=1e-4, rank_init=8, block_size=16, operator_form=form)
     slv.set_instance(inst)
     info = slv.solve()
     assert info.status == pkg.CONVERGED, info.as_dict()

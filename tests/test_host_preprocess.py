@@ -98,3 +98,15 @@ def test_malformed_input_is_rejected(pkg, bad):
     with pytest.raises(pkg.ProxSDPError) as e:
         pkg.analyze_problem(n, m_eq, ptr, col, val, rhs, **kw)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("form,ok", [(0, True), (1, True), (2, True), (3, False), (-1, False)])
+def test_operator_form_setting_validated(pkg, form, ok):
+    inst = si.maxcut_er(30, 0.2, 1)
+    s = pkg.default_settings(operator_form=form)
+    if ok:
+        _analyze(pkg, inst, settings=s)
+    else:
+        with pytest.raises(pkg.ProxSDPError) as e:
+            _analyze(pkg, inst, settings=s)
+        assert e.value.code == -1
