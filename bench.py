@@ -368,6 +368,75 @@ def run_mimo_batch(args):
     return 0
 
 
+SWEEPS = {
+    # Table 2 shape: sensor network localisation (Sec. 5.2), n sensors, 5 anchors, radius 0.3
+    "table2": ("sensor network localisation (Sec. 5.2), Table 2 sizes", [50, 100, 150, 200, 250, 300]),
+    # Table 3 shape: MIMO detection with high SNR (Sec. 5.3, noise variance 0.01), signal length n
+    "table3": ("MIMO detection, high SNR (Sec. 5.3), Table 3 sizes", [100, 500, 1000, 2000]),
+}
+# LR-PD-SDP running times (s) printed in the paper's Table 2 and Table 3 (a
+# CPU implementation on other hardware): context beside each size, not a target
+PAPER_SECONDS = {
+    "table2": {50: 0.6, 100: 1.6, 150: 3.6, 200: 6.1, 250: 7.9, 300: 13.5},
+    "table3": {100: 0.1, 500: 1.1, 1000: 4.7, 2000: 38.9, 3000: 122.1, 4000: 258.3, 5000: 472.4},
+}
+
+
+def sweep_instance(kind, n, seed):
+    import numpy as np
+
+    import sdp_instances as si
+
+    if kind == "table2":
+        return si.sensor_network(n, 5, 0.3, seed=seed)
+    return si.mimo(n, np.random.default_rng(seed), snr_noise_var=0.01)
+
+
+def run_sweep(args):
+    """One seeded instance per size, solved once to 1e-4 (after one untimed
+    solve of the smallest size); the line lists time to tolerance per size."""
+    import torch
+
+    import paper_1810_05231_gb300 as pkg
+
+    title, sizes = SWEEPS[args.workload]
+    if args.sizes:
+        sizes = [int(v) for v in args.sizes.split(",")]
+    rank0 = 4 if args.workload == "table2" else 2
+
+    def solve(n):
+        inst = sweep_instance(args.workload, n, seed=n)
+        slv = pkg.Solver(tol=1e-4, rank_init=rank0, max_iter=10 ** 7, time_limit_s=args.time_limit,
+                         check_every=200)
+        t0 = time.perf_counter()
+        slv.set_instance(inst)
+        info = slv.solve()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        slv.close()
+        return inst.n, info, wall
+
+    solve(sizes[0])
+    rows = []
+    for n in sizes:
+        dim, info, wall = solve(n)
+        rows.append({"n": n, "matrix_dim": dim, "status": info.status, "converged": info.status == pkg.CONVERGED,
+                     "time_to_tol_s": round(info.solve_seconds, 4), "wall_s_with_set_problem": round(wall, 4),
+                     "iters": int(info.iters), "final_rank": info.final_rank, "primal_obj": info.primal_obj,
+                     "rel_primal_res": info.rel_primal_res, "rel_dual_res": info.rel_dual_res,
+                     "rel_gap": info.rel_gap, "gpu_launches": int(info.kernel_launches),
+                     "paper_lr_pd_sdp_s": PAPER_SECONDS[args.workload].get(n)})
+    total = sum(r["time_to_tol_s"] for r in rows)
+    line = {"metric": f"time to 1e-4 per instance size: {title}", "value": round(total, 4), "unit": "s",
+            "n_gpus": 1, "steps": len(rows), "warmup": 1, "ms_per_step": round(1000 * total / len(rows), 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.workload, "tol": 1e-4, "rank_init": rank0,
+                                            "time_limit_s": args.time_limit},
+            "sweep": rows, "gpu_launches": int(sum(r["gpu_launches"] for r in rows))}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +445,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--full-eig-iters", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"])
+    ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"] + sorted(SWEEPS))
+    ap.add_argument("--sizes", default="", help="comma-separated sizes for the table2 / table3 sweeps")
+    ap.add_argument("--time-limit", type=float, default=60.0, help="per-instance cap of the sweeps (s)")
     ap.add_argument("--operator", default="explicit", choices=sorted(OPERATOR_FORMS),
                     help="how the projection applies S^k: formed in HBM, or from the factors of X^k")
     ap.add_argument("--other-operator", default="factored", choices=sorted(OPERATOR_FORMS) + ["none"],
@@ -386,6 +457,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "mimo-batch":
         return run_mimo_batch(args)
+    if args.workload in SWEEPS:
+        return run_sweep(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 

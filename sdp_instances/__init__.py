@@ -203,8 +203,12 @@ def sensor_network(n_sensors: int, n_anchors: int, radius: float, seed: int, d: 
                                 n_ss=len(si), n_as=len(ak)))
 
 
-def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1) -> SDPProblem:
-    """Binary least-squares (MIMO detection) SDR of Sec. 5.3, diag(X)=1 only."""
+def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1, box: bool = False) -> SDPProblem:
+    """Binary least-squares (MIMO detection) SDR of Sec. 5.3: diag(X) = 1 and,
+    with ``box``, the paper's elementwise bounds -1 <= X_ij <= 1 for i < j as
+    2 * n(n-1)/2 inequality rows (X_ij <= 1 and -X_ij <= 1; the diagonal is
+    fixed by the equality rows).  Each row holds one off-diagonal svec entry
+    of value +-1/2, so tr(A X) = +-X_ij."""
     H = rng.normal(0.0, np.sqrt(1.0 / N), (N, N))
     x = rng.choice(np.array([-1.0, 1.0]), N)
     s = H @ x + rng.normal(0.0, np.sqrt(snr_noise_var), N)
@@ -215,8 +219,17 @@ def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1) -> SDPPro
     C[N, :N] = C[:N, N]
     C[N, N] = s @ s
     ptr, col, val = _diag_rows(n)
-    return SDPProblem(n=n, m_eq=n, A_rowptr=ptr, A_col=col, A_val=val, rhs=np.ones(n),
-                      C_dense=C, meta=dict(kind="mimo", H=H, x=x, s=s))
+    rhs = np.ones(n)
+    if box:
+        iu, ju = np.triu_indices(n, 1)
+        k = iu.shape[0]
+        cols = svec_index(iu, ju)
+        col = np.concatenate([col, cols, cols])
+        val = np.concatenate([val, np.full(k, 0.5), np.full(k, -0.5)])
+        ptr = np.concatenate([ptr, ptr[-1] + np.arange(1, 2 * k + 1, dtype=np.int64)])
+        rhs = np.concatenate([rhs, np.ones(2 * k)])
+    return SDPProblem(n=n, m_eq=n, A_rowptr=ptr, A_col=col, A_val=val, rhs=rhs,
+                      C_dense=C, meta=dict(kind="mimo", H=H, x=x, s=s, box=box))
 
 
 # ---------------------------------------------------------------------------

@@ -266,6 +266,46 @@ def test_inequality_rows(pkg):
     slv.close()
 
 
+def test_mimo_box_rows_small_against_oracle(pkg):
+    """Sec. 5.3 MIMO SDR with the elementwise bounds -1 <= X_ij <= 1 as
+    2 * 300 inequality rows (n = 25, dense projection), against the oracle."""
+    inst = si.mimo(24, np.random.default_rng(5), box=True)
+    prob = Problem.from_instance(inst)
+    ref = oracle.solve(prob, mode="lr", tol=1e-6, rank_init=2, max_iter=200000)
+    assert ref.status == 0
+    slv = pkg.Solver(tol=1e-5, rank_init=2, max_iter=200000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - ref.pobj) <= 1e-4 * (1 + abs(ref.pobj))
+    got = slv.get_primal_dual()
+    assert np.all(got["y"][inst.m_eq:] <= 1e-12)  # paper's sign: y_ineq <= 0
+    cert = oracle.certificates(prob, got["X"], -got["y"])
+    assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 1e-4
+    slv.close()
+
+
+def test_mimo_box_rows_lanczos_path(pkg):
+    """n = 151 (block Krylov path) with 2 * 11 325 box rows.  The bounds are
+    implied by diag(X) = 1 and X psd (|X_ij| <= sqrt(X_ii X_jj)), so the
+    optimum equals the one without them."""
+    res = {}
+    for box in (False, True):
+        inst = si.mimo(150, np.random.default_rng(8), box=box)
+        slv = pkg.Solver(tol=1e-4, rank_init=2, max_iter=400000)
+        slv.set_instance(inst)
+        info = slv.solve()
+        assert info.status == pkg.CONVERGED, (box, info.as_dict())
+        res[box] = (info, slv.get_primal_dual(), inst)
+        slv.close()
+    p0, p1 = res[False][0].primal_obj, res[True][0].primal_obj
+    assert abs(p1 - p0) <= 3e-4 * (1 + abs(p0)), (p0, p1)
+    info, got, inst = res[True]
+    assert np.all(got["y"][inst.m_eq:] <= 1e-12)
+    cert = oracle.certificates(Problem.from_instance(inst), got["X"], -got["y"])
+    assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 2e-4, cert
+
+
 # ---------------------------------------------------------------------------
 # the n = 2000 MaxCut workload (weights 1..5), certified at full size
 # ---------------------------------------------------------------------------

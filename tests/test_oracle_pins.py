@@ -301,6 +301,23 @@ def test_mimo_relaxation_bounds_brute_force():
         np.testing.assert_array_equal(xs, xbest)
 
 
+def test_mimo_box_rows_are_redundant():
+    """The paper's MIMO SDR adds -1 <= X_ij <= 1 (Sec. 5.3).  With diag(X) = 1
+    and X psd, |X_ij| <= sqrt(X_ii X_jj) = 1 already, so the bounds cut nothing:
+    the optimum is the one without them.  The 2 n(n-1)/2 inequality rows keep
+    non-negative multipliers (algorithm sign) and are satisfied."""
+    no_box = Problem.from_instance(si.mimo(8, np.random.default_rng(5)))
+    box = Problem.from_instance(si.mimo(8, np.random.default_rng(5), box=True))
+    assert box.M.m == 9 + 2 * 36
+    r0 = oracle.solve(no_box, mode="lr", tol=1e-7, rank_init=2, max_iter=200000)
+    r1 = oracle.solve(box, mode="lr", tol=1e-7, rank_init=2, max_iter=200000)
+    assert r0.status == 0 and r1.status == 0
+    assert abs(r1.pobj - r0.pobj) <= 1e-5 * (1 + abs(r0.pobj))
+    assert np.all(r1.y[box.m_eq:] >= 0.0)
+    cert = oracle.certificates(box, r1.X, r1.y)
+    assert cert["primal_ineq"] < 1e-6 and cert["rel_gap"] < 1e-5
+
+
 # ---------------------------------------------------------------------------
 # certificates and the rank rule
 # ---------------------------------------------------------------------------
