@@ -58,8 +58,9 @@ struct DF {
 // S * Q block product (SIMT, inner dimension split across a thread-block cluster)
 // ---------------------------------------------------------------------------
 // CTA tile: 128 rows of S x up to 64 columns of Q over one slice of the inner
-// dimension, in chunks of 32.  The S chunk is staged transposed (Ss[k][row])
-// so a thread reads its 8 rows as two float4 broadcasts; each thread holds
+// dimension, in chunks of 32.  The S chunk is staged transposed (Ss[k][row],
+// the 4-row groups of row k permuted by XOR with k & 28 against bank
+// conflicts) so a thread reads its 8 rows as two float4 broadcasts; each thread holds
 // 8 rows x G columns (G = column groups of 16).  The `ns` slices of a row
 // block form one cluster: their partial tiles stay in shared memory and, after
 // a cluster barrier, CTA c of the cluster sums rows [c*128/ns, (c+1)*128/ns)
@@ -79,13 +80,16 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
   if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
     cudaGraphSetConditional(cond, 1u);
   // staging (S chunk, Q chunk) and, after the main loop, this CTA's partial
-  // tile (column-major, 16G x 128) share one buffer
+  // tile (row-major, 128 x 16G, row stride 16G + 2: the two rows a warp
+  // stores per column group land 16 banks apart, so the stores are
+  // conflict-free) share one buffer
   constexpr int kStage = MV_KC * MV_LDS + MV_KC * (16 * G + 1);
-  constexpr int kPart = 16 * G * MV_RB;
+  constexpr int kLdp = 16 * G + 2;
+  constexpr int kPart = MV_RB * kLdp;
   __shared__ __align__(16) float smbuf[kStage > kPart ? kStage : kPart];
   float(*Ss)[MV_LDS] = reinterpret_cast<float(*)[MV_LDS]>(smbuf);
   float(*Qs)[16 * G + 1] = reinterpret_cast<float(*)[16 * G + 1]>(smbuf + MV_KC * MV_LDS);
-  float(*Ps)[MV_RB] = reinterpret_cast<float(*)[MV_RB]>(smbuf);
+  float(*Ps)[kLdp] = reinterpret_cast<float(*)[kLdp]>(smbuf);
   const int tid = threadIdx.x;
   const int tc = tid & 15, tr = tid >> 4;  // column within group, row group (8 rows)
   const int ns = gridDim.x;                // slices = cluster size
@@ -149,11 +153,15 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int idx = tid + 256 * v;
+      // row k of the transposed chunk holds S row rr at column rr ^ (k & 28)
+      // (4-float groups permuted by the row: conflict-free transposed stores,
+      // float4 reads stay aligned)
       const int rr = idx >> 3, kq = (idx & 7) * 4;
-      Ss[kq][rr] = sreg[v].x;
-      Ss[kq + 1][rr] = sreg[v].y;
-      Ss[kq + 2][rr] = sreg[v].z;
-      Ss[kq + 3][rr] = sreg[v].w;
+      const int cs = rr ^ kq;
+      Ss[kq][cs] = sreg[v].x;
+      Ss[kq + 1][cs] = sreg[v].y;
+      Ss[kq + 2][cs] = sreg[v].z;
+      Ss[kq + 3][cs] = sreg[v].w;
     }
 #pragma unroll
     for (int v = 0; v < QV; ++v) {
@@ -174,8 +182,8 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
     if (k0 + MV_KC < ke) load_chunk(k0 + MV_KC);  // in flight during the compute below
 #pragma unroll 4
     for (int kk = 0; kk < MV_KC; ++kk) {
-      const float4 s0 = *reinterpret_cast<const float4*>(&Ss[kk][tr * 8]);
-      const float4 s1 = *reinterpret_cast<const float4*>(&Ss[kk][tr * 8 + 4]);
+      const float4 s0 = *reinterpret_cast<const float4*>(&Ss[kk][(tr * 8) ^ (kk & 28)]);
+      const float4 s1 = *reinterpret_cast<const float4*>(&Ss[kk][(tr * 8 + 4) ^ (kk & 28)]);
       const float sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
 #pragma unroll
       for (int g = 0; g < G; ++g) {
@@ -202,18 +210,20 @@ __global__ void __launch_bounds__(256) k_block_matvec(const float* __restrict__ 
 #pragma unroll
   for (int g = 0; g < G; ++g)
 #pragma unroll
-    for (int a = 0; a < 8; ++a) Ps[tc + 16 * g][tr * 8 + a] = acc[a][g];
+    for (int a = 0; a < 8; ++a) Ps[tr * 8 + a][tc + 16 * g] = acc[a][g];
   cg::cluster_group cluster = cg::this_cluster();
   cluster.sync();
   const int rank = (int)cluster.block_rank();
   const int rows_per = MV_RB / ns;
   for (int idx = tid; idx < kc * rows_per; idx += 256) {
     const int col = idx / rows_per, rr = rank * rows_per + idx % rows_per;
+    // all remote loads issued before the additions (slice order kept)
+    float v[16];
+#pragma unroll
+    for (int sl = 0; sl < 16; ++sl) v[sl] = (sl < ns) ? cluster.map_shared_rank(&Ps[0][0], sl)[rr * kLdp + col] : 0.f;
     float sum = 0.f;
-    for (int sl = 0; sl < ns; ++sl) {
-      const float* rp = cluster.map_shared_rank(&Ps[0][0], sl);
-      sum += rp[col * MV_RB + rr];
-    }
+#pragma unroll
+    for (int sl = 0; sl < 16; ++sl) sum += v[sl];
     const int row = r0 + rr;
     if (row < n) W[(size_t)(c0 + col) * ldw + row] = sum;
   }
