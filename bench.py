@@ -531,7 +531,7 @@ def main():
                 "d2h_bytes_per_step": int(res["d2h"]),
                 "time_to_tol_s": round(statistics.median(res["e2e_times"]), 5)},
         "roofline": res["roofline"],
-        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.54, "bound": "latency (one CTA)",
+        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.534, "bound": "latency (one CTA)",
                             "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
         "cpu_baseline": cpu, "clocks": res["clocks"],
         "gpu_launches": int(res["launches"]), "full_eig": res["full"], "other_operator_form": res["alt"],
