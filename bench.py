@@ -437,6 +437,21 @@ def run_sweep(args):
     return 0
 
 
+def aggregate_replicas(total_t, total_it, device):
+    """Whole-job figures of N independent replicas (one per rank, no data-path
+    collective): iterations summed over the ranks, time the maximum over the
+    ranks (the slowest replica ends the job).  `device` is "cuda" under NCCL,
+    "cpu" under gloo."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(total_t)], dtype=torch.float64, device=device)
+    it = torch.tensor([float(total_it)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(it.item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,14 +511,7 @@ def main():
     total_t = sum(res["times"])
     total_it = sum(res["iters"])
     if world > 1:
-        import torch
-        import torch.distributed as dist
-
-        t = torch.tensor([total_t], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        it = torch.tensor([float(total_it)], device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        total_t, total_it = float(t.item()), float(it.item())
+        total_t, total_it = aggregate_replicas(total_t, total_it, "cuda")
     cpu = None
     if rank == 0 and world == 1:
         v, k, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
