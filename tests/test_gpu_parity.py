@@ -306,6 +306,40 @@ def test_mimo_box_rows_lanczos_path(pkg):
     assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 2e-4, cert
 
 
+def test_sensor_positions_small(pkg):
+    """Exact distances, every pair in range (n = 12, dense projection): the SDR
+    is exact, Z has rank 2 and its block holds the true positions."""
+    inst = si.sensor_network(10, 4, 2.0, seed=2)
+    slv = pkg.Solver(tol=1e-6, rank_init=4, max_iter=400000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    Z = slv.get_primal_dual()["X"]
+    slv.close()
+    rmse = np.sqrt(np.mean((Z[:2, 2:].T - inst.meta["sensors"]) ** 2))
+    assert rmse < 1e-3, rmse
+    lam = np.linalg.eigvalsh(Z)[::-1]
+    assert lam[2] < 1e-3 * lam[0]
+
+
+def test_sensor_positions_lanczos_path(pkg):
+    """130 sensors, 5 anchors, every pair in range (n = 132, block Krylov path),
+    20 000 iterations: the FP64 oracle's LR-PD-SDP reaches position RMSE 5.9e-4
+    and rank 2 after the same count, so the GPU iterate must recover the
+    positions to 2e-3 with a rank-2 Z."""
+    inst = si.sensor_network(130, 5, 2.0, seed=4)
+    slv = pkg.Solver(tol=1e-6, rank_init=4, max_iter=20000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status in (pkg.CONVERGED, pkg.MAX_ITER), info.as_dict()
+    Z = slv.get_primal_dual()["X"]
+    slv.close()
+    rmse = np.sqrt(np.mean((Z[:2, 2:].T - inst.meta["sensors"]) ** 2))
+    assert rmse < 2e-3, rmse
+    lam = np.linalg.eigvalsh(Z)[::-1]
+    assert lam[2] < 1e-3 * lam[0]
+
+
 # ---------------------------------------------------------------------------
 # the n = 2000 MaxCut workload (weights 1..5), certified at full size
 # ---------------------------------------------------------------------------

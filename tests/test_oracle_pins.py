@@ -318,6 +318,21 @@ def test_mimo_box_rows_are_redundant():
     assert cert["primal_ineq"] < 1e-6 and cert["rel_gap"] < 1e-5
 
 
+@pytest.mark.parametrize("ns,na,radius,seed", [(8, 4, 2.0, 1), (10, 4, 2.0, 2), (12, 5, 0.9, 3)])
+def test_sensor_positions_recovered_exactly(ns, na, radius, seed):
+    """Sensor localisation (Sec. 5.2) with exact distances on a uniquely
+    realisable network (every pair in range, or radius 0.9 in the unit square
+    with 5 anchors): the SDR is exact, so the solution Z = [I X; X^T Y] has
+    rank d = 2 and its block X holds the true sensor positions."""
+    inst = si.sensor_network(ns, na, radius, seed=seed)
+    res = oracle.solve(Problem.from_instance(inst), mode="full", tol=1e-8, max_iter=400000)
+    assert res.status == 0
+    pos = res.X[:2, 2:].T
+    assert np.sqrt(np.mean((pos - inst.meta["sensors"]) ** 2)) < 1e-6
+    lam = np.linalg.eigvalsh(res.X)[::-1]
+    assert lam[2] < 1e-6 * lam[0] and lam[1] > 1e-2 * lam[0]
+
+
 # ---------------------------------------------------------------------------
 # certificates and the rank rule
 # ---------------------------------------------------------------------------
