@@ -322,6 +322,44 @@ def cpu_oracle_sample(seconds=15.0, min_iters=2):
     return k / dt, k, dt
 
 
+def host_description():
+    """CPU model, hardware threads and the BLAS numpy links (for the oracle's timing)."""
+    import platform
+
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")) and ":" in line:
+                    model = line.split(":", 1)[1].strip() or model
+                    if line.lower().startswith("model name"):
+                        break
+    except OSError:
+        pass
+    blas = "unknown"
+    try:
+        cfg = np.show_config(mode="dicts")
+        b = cfg["Build Dependencies"]["blas"]
+        blas = f'{b.get("name", "?")} {b.get("version", "")}'.strip()
+    except Exception:
+        pass
+    return {"cpu": f"{platform.machine()} {model}", "nproc": os.cpu_count(), "blas": blas,
+            "blas_threads": os.environ.get("OMP_NUM_THREADS", "default (all cores)")}
+
+
+def projection_hbm(n, info, iters_per_s, hbm_gbs):
+    """HBM share of the projection per iteration: (q + 1) n^2 4 bytes (q block
+    products reading S, one rebuild writing it; full n^2, not the symmetric
+    half) over the measured time of a whole iteration (an upper bound on the
+    projection's time, so the fraction is a lower bound)."""
+    q = info["matvecs"] / max(info["iters"], 1)
+    bytes_per_iter = (q + 1.0) * n * n * 4.0
+    gbs = bytes_per_iter * iters_per_s / 1e9
+    return {"bytes_per_iter": round(bytes_per_iter), "q_products_per_iter": round(q, 3),
+            "achieved_gbs": round(gbs, 1), "peak_gbs": hbm_gbs, "frac": round(gbs / hbm_gbs, 4),
+            "time_base": "whole iteration"}
+
+
 def run_mimo_batch(args):
     """Aggregate solves/s of the MIMO batch (row a12), inputs resident."""
     # more hardware work queues than the default 8, so that the instances'
@@ -516,7 +554,8 @@ def main():
     if rank == 0 and world == 1:
         v, k, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
         cpu = {"value": round(v, 4), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{k} LR-PD-SDP iterations of the n=2000 workload (FP64, exact eigh) in {dt:.1f} s"}
+               "sample": f"{k} LR-PD-SDP iterations of the n=2000 workload (FP64, exact eigh) in {dt:.1f} s",
+               "host": host_description()}
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -539,6 +578,7 @@ def main():
                 "d2h_bytes_per_step": int(res["d2h"]),
                 "time_to_tol_s": round(statistics.median(res["e2e_times"]), 5)},
         "roofline": res["roofline"],
+        "projection_hbm": projection_hbm(2000, info, value, _peaks()[0]),
         "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.534, "bound": "latency (one CTA)",
                             "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
         "cpu_baseline": cpu, "clocks": res["clocks"],
