@@ -560,11 +560,12 @@ void launch_apply_rinv(float* Z, int ldz, int w, const float* Rinv, const int* f
 //     of T - x I): one count per thread at evenly spaced points of the
 //     Gershgorin interval brackets every eigenvalue, then G threads per
 //     eigenvalue narrow its bracket by multisection.
-// (3) Eigenvectors of the tridiagonal matrix by inverse iteration: three
+// (3) Eigenvectors of the tridiagonal matrix by inverse iteration: two
 //     solves with the partially pivoted LU factorisation of T - lambda I from
-//     a pseudo-random start.  Eigenvalues closer than 1e-3 ||T|| form a group
-//     that one thread handles, orthogonalising each member against the
-//     previous ones after every solve (modified Gram-Schmidt).
+//     a pseudo-random start, one thread per isolated eigenvalue.  Eigenvalues
+//     closer than kSeGroupTol ||T|| form a group that one warp handles (a lane
+//     per member), orthogonalising each member against the previous ones after
+//     every solve (modified Gram-Schmidt).
 // (4) Back-transformation Y = H_0 H_1 ... H_{K-3} Z.
 // (5) One refinement step for the `nout` wanted eigenvectors (Ogita & Aishima,
 //     "Iterative refinement for symmetric eigenvalue decomposition", 2018):
@@ -1076,7 +1077,9 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     s_ng = ng;
   }
   __syncthreads();
-  {  // isolated eigenvalues: one thread each, three solves; LU factors in
+  {  // isolated eigenvalues: one thread each, two solves (each multiplies the
+     // wanted component by at least gap / |lambda error| > 100 against any
+     // other: eigenvalues closer than kSeGroupTol go to the group path); LU factors in
      // shared-memory slots (the refinement scratch), in batches of ns
     const int nwords = (K + 31) / 32;
     const int ns = min(nth, (int)((Kp * (Kp + 1) / 2 + 2 * Kp * JB) / (2 * K + nwords)));
@@ -1090,7 +1093,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
         float* x = V + b;  // column b, stride ld
         for (int i = 0; i < K; ++i)
           x[i * ld] = hash_uniform(0x5EEDULL + (unsigned long long)b, (unsigned long long)i, 77ULL);
-        for (int it = 0; it < 3; ++it) {
+        for (int it = 0; it < 2; ++it) {
           tri_solve_slot(td, te, K, lam[b], lm, rp, swb, ns, tid, x, ld);
           float mx = 0.f;
           for (int i = 0; i < K; ++i) mx = fmaxf(mx, fabsf(x[i * ld]));
