@@ -579,7 +579,7 @@ def main():
                 "time_to_tol_s": round(statistics.median(res["e2e_times"]), 5)},
         "roofline": res["roofline"],
         "projection_hbm": projection_hbm(2000, info, value, _peaks()[0]),
-        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.534, "bound": "latency (one CTA)",
+        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.516, "bound": "latency (one CTA)",
                             "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
         "cpu_baseline": cpu, "clocks": res["clocks"],
         "gpu_launches": int(res["launches"]), "full_eig": res["full"], "other_operator_form": res["alt"],
