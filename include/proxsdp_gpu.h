@@ -148,7 +148,10 @@ int proxsdp_gpu_create(const proxsdp_gpu_settings* settings, int device, void* c
  * for a dense a*11^T row).  rhs = [b; h] (m_total).  Validates everything
  * (sorted-or-not, in-range indices, finite values) and returns
  * PROXSDP_ERR_INVALID_ARG on malformed input; copies the data to the device,
- * scales rows (settings.normalize_rows) and computes ||M||_2 and alpha. */
+ * scales rows (settings.normalize_rows) and computes ||M||_2 and alpha.
+ * Device memory: O(n*128 + nnz) for the Krylov basis, the factors and the
+ * sparse data, plus n * ceil(n/32)*32 floats for S unless the factored
+ * operator form applies (operator_form); PROXSDP_ERR_OOM when it does not fit. */
 int proxsdp_gpu_set_problem(proxsdp_gpu_t h, int64_t n, const double* C_dense, int64_t c_nnz,
                             const int64_t* c_idx, const double* c_val, int64_t m_total,
                             int64_t m_eq, const int64_t* A_rowptr, const int64_t* A_col,
