@@ -182,14 +182,15 @@ def run_ours(args, rank, world):
             e2e_iters.append(info.iters)
             d2h = out["y"].nbytes + out["V"].nbytes + out["lam"].nbytes
         slv2.close()
-    roof = roofline(pkg, torch, stream, n, infos[-1])
-    full = full_eig_baseline(torch, inst, stream, iters=args.full_eig_iters) if args.full_eig_iters > 0 else None
+    roof = block_product_roofline(pkg, torch, stream, STREAM_N, 48)
+    stream_leg = streaming_leg(pkg, torch, stream) if args.streaming else None
+    full = full_eig_baseline(torch, inst, stream, cap_s=args.full_eig_cap) if args.full_eig_cap > 0 else None
     other = args.other_operator
     alt = (operator_form_run(pkg, torch, stream, inst, flush, other, args.steps, min(args.warmup, 2))
            if other != "none" and other != args.operator else None)
     res = dict(times=times, iters=iters, infos=infos, clocks=clk, e2e_times=e2e_times, e2e_iters=e2e_iters,
                h2d=h2d, d2h=d2h, roofline=roof, full=full, launches=sum(i["kernel_launches"] for i in infos),
-               alt=alt)
+               alt=alt, streaming=stream_leg)
     slv.close()
     return res
 
@@ -220,30 +221,32 @@ def operator_form_run(pkg, torch, stream, inst, flush, operator, steps, warmup):
             "final_rank": info.final_rank, "rel_gap": info.rel_gap, "gpu_launches": int(launches)}
 
 
-def roofline(pkg, torch, stream, n, info):
-    """Time the block product S * Q alone (cold L2) and place it on the roofline.
+STREAM_N = 16384
+STREAM_WORKLOAD = "maxcut_er_n16384_p0.001_unit_seed5"
 
-    Per launch it moves n^2 * 4 bytes of S plus 2 * n * k * 4 bytes of Q and W
-    (algorithmic bytes) and performs 2 * n^2 * k flops; k is the Krylov block
-    width the solve uses at its final rank r, 16 * ceil((r + max(8, r/4)) / 16).
-    With k = 48 the intensity is 24 flop/byte, above the FP32 SIMT ridge
-    (80.6 TFLOP/s / 6.78 TB/s = 11.9 flop/byte), so the kernel is bound by
-    FP32 arithmetic ("alu"): peak = 152 SMs x 128 FP32 lanes x 2 flop x
-    2.07 GHz = 80.6 TFLOP/s.  The HBM view is reported beside it.
+
+def block_product_roofline(pkg, torch, stream, n, k, launches=20):
+    """Time the block product W = S Q alone and place it on the HBM roofline.
+
+    Per launch it reads S once (n^2 * 4 bytes, FP32) and Q (n * k * 4) and
+    writes W (n * k * 4): algorithmic bytes n^2 * 4 + 2 * n * k * 4.  At
+    n = 16384 S is 1 GiB, far larger than the 129 MB L2, so every launch
+    streams S from HBM (no flush needed).  achieved = algorithmic bytes /
+    mean CUDA-event time of one launch on the launching stream; peak = the
+    measured copy bandwidth of MEASURED_PEAKS.json.
     """
     hbm, _, src = _peaks()
-    r = int(info["final_rank"])
-    k = min(64, 16 * ((r + max(8, r // 4) + 15) // 16))
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     S = torch.randn(n, n, device="cuda", generator=g)
     S = (S + S.t()) * 0.5
     Q = torch.randn(k, n, device="cuda", generator=g)
-    flush = torch.zeros(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    flush = torch.zeros(128 * 1024 * 1024, dtype=torch.float32, device="cuda") if n * n * 4 < 512 << 20 else None
     durs = []
     with torch.cuda.stream(stream):
-        for it in range(23):
-            flush.add_(1.0)
+        for it in range(launches + 3):
+            if flush is not None:
+                flush.add_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -252,11 +255,10 @@ def roofline(pkg, torch, stream, n, info):
             e1.synchronize()
             if it >= 3:
                 durs.append(e0.elapsed_time(e1) * 1e-3)
+    del S, Q, flush
+    torch.cuda.empty_cache()
     t = statistics.mean(durs)
     bytes_alg = n * n * 4 + 2 * n * k * 4
-    flops = 2.0 * n * n * k
-    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12  # TFLOP/s, FP32 FMA lanes at the maximum SM clock
-    achieved = flops / t / 1e12
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
@@ -264,39 +266,111 @@ def roofline(pkg, torch, stream, n, info):
             traffic = json.load(open(tp)).get(f"k_block_matvec_n{n}_k{k}")
         except Exception:
             traffic = None
-    return {"kernel": "k_block_matvec", "bound": "alu", "achieved": round(achieved, 2), "peak": round(alu_peak, 2),
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz", "unit": "TFLOP/s",
-            "frac": round(achieved / alu_peak, 4), "traffic": traffic, "alg_bytes_per_launch": bytes_alg,
-            "flops_per_launch": flops, "avg_launch_s": t, "k": k,
-            "hbm_achieved_gbs": round(bytes_alg / t / 1e9, 1), "hbm_peak_gbs": hbm, "hbm_peak_source": src,
-            "hbm_frac": round(bytes_alg / t / 1e9 / hbm, 4), "l2": "flushed before each launch"}
+    achieved = bytes_alg / t / 1e9
+    return {"kernel": "k_block_matvec", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+            "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
+            "n": n, "k": k, "alg_bytes_per_launch": bytes_alg, "avg_launch_s": t, "launches_timed": len(durs),
+            "flops_per_launch": 2.0 * n * n * k, "tflops": round(2.0 * n * n * k / t / 1e12, 2),
+            "l2": "S larger than L2" if flush is None else "flushed before each launch"}
 
 
-def full_eig_baseline(torch, inst, stream, iters=10):
-    """Alg. 1 with torch.linalg.eigh (vendor library) in FP32 on the same GPU:
-    per-iteration time of the full-projection PDHG, for comparison only."""
-    import oracle  # noqa: F401  (problem data only; no oracle arithmetic is timed here)
+def streaming_leg(pkg, torch, stream, iters=30, warmup=10):
+    """The LR-PD-SDP iteration where S^k streams from HBM: MaxCut of
+    G(16384, 0.001) (unit weights, seed 5), S^k formed in HBM (1 GiB FP32),
+    rank fixed at 32 (block width 48).  `warmup` untimed iterations, then
+    `iters` iterations timed with CUDA events on the solver's stream.  The
+    projection's algorithmic bytes per iteration are (q + 1) n^2 4 (q block
+    products reading S, one rebuild writing it); over the whole iteration
+    time they give a lower bound on the projection's HBM fraction."""
+    import sdp_instances as si
+
+    hbm = _peaks()[0]
+    inst = si.maxcut_er_streaming(STREAM_N)
+    n = inst.n
+    with torch.cuda.stream(stream):
+        slv = pkg.Solver(settings_for(pkg, "explicit", tol=1e-12, rank_init=32, max_rank=32, check_every=10),
+                         stream=stream.cuda_stream)
+        slv.set_instance(inst)
+        i0 = slv.iterate(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        i1 = slv.iterate(iters)
+        e1.record(stream)
+        e1.synchronize()
+        slv.close()
+    t = e0.elapsed_time(e1) * 1e-3
+    done = int(i1.iters - i0.iters)
+    q = (i1.matvecs - i0.matvecs) / max(done, 1)
+    bytes_iter = (q + 1.0) * n * n * 4.0
+    gbs = bytes_iter * done / t / 1e9
+    return {"workload": STREAM_WORKLOAD, "n": n, "rank": 32, "iters_timed": done, "iters_per_s": round(done / t, 2),
+            "ms_per_iter": round(1000 * t / max(done, 1), 4), "q_products_per_iter": round(q, 3),
+            "projection_bytes_per_iter": round(bytes_iter), "projection_gbs_over_iteration": round(gbs, 1),
+            "projection_frac_lower_bound": round(gbs / hbm, 4), "status": int(i1.status),
+            "gpu_launches": int(i1.kernel_launches - i0.kernel_launches)}
+
+
+def full_eig_baseline(torch, inst, stream, cap_s=60.0, tol=1e-4, rate_iters_fp64=5):
+    """Alg. 1 (PD-SDP, exact projection) with the vendor eigensolver
+    (torch.linalg.eigh, cuSOLVER) on the same GPU: the comparison baseline of
+    the metric, not part of the library.  The MaxCut workload has only the
+    constraints diag(X) = 1 (||A_i||_F = 1, ||M||_2 = 1, alpha = 0.95), so
+    M(X) = diag(X) and M*(y) = Diag(y).  Same stop test as the library
+    (relative residuals of Sec. 2.2 and relative gap <= tol), in FP32 from
+    X = 0, y = 0, capped at `cap_s` seconds; the FP64 eigensolver's
+    per-iteration time is reported beside it."""
     n = inst.n
     dev = torch.device("cuda")
-    C = torch.tensor(inst.c_dense(), dtype=torch.float32, device=dev)
-    alpha = 0.95  # diagonal constraints: ||M||_2 = 1
-    X = torch.zeros(n, n, device=dev)
-    y = torch.zeros(n, device=dev)
-    with torch.cuda.stream(stream):
-        for it in range(iters + 2):
-            if it == 2:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-            S = X - alpha * (C + torch.diag(y))
-            lam, U = torch.linalg.eigh(S)
-            Xn = (U * lam.clamp(min=0)) @ U.t()
-            yh = y + alpha * torch.diagonal(2 * Xn - X)
-            y = yh - alpha
-            X = Xn
-        torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / iters
-    return {"impl": "torch.linalg.eigh FP32 (cuSOLVER), Alg. 1", "iters_per_s": round(1.0 / dt, 2),
-            "s_per_iter": dt, "iters_timed": iters}
+
+    def run(dtype, max_s, max_iters):
+        C = torch.tensor(inst.c_dense(), dtype=dtype, device=dev)
+        normC = float(torch.linalg.norm(C))
+        b = torch.ones(n, dtype=dtype, device=dev)
+        normb = float(torch.linalg.norm(b))
+        alpha = 0.95
+        X = torch.zeros(n, n, dtype=dtype, device=dev)
+        y = torch.zeros(n, dtype=dtype, device=dev)
+        res = None
+        with torch.cuda.stream(stream):
+            torch.linalg.eigh(X)  # solver workspace set-up, outside the timed loop
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it = 0
+            while True:
+                it += 1
+                S = X - alpha * (C + torch.diag(y))
+                lam, U = torch.linalg.eigh(S)
+                Xn = (U * lam.clamp(min=0)) @ U.t()
+                yn = y + alpha * torch.diagonal(2 * Xn - X) - alpha * b
+                dX = Xn - X
+                dy = yn - y
+                eps_p = torch.linalg.norm(dX / alpha - torch.diag(dy))
+                eps_d = torch.linalg.norm(dy / alpha - torch.diagonal(dX))
+                pobj = torch.sum(C * Xn)
+                dobj = -torch.dot(b, yn)
+                X, y = Xn, yn
+                if it % 10 == 0 or it >= max_iters:
+                    vals = torch.stack([eps_p, eps_d, pobj, dobj]).double().cpu().tolist()
+                    rel_p, rel_d = vals[0] / (1 + normC), vals[1] / (1 + normb)
+                    gap = abs(vals[2] - vals[3]) / (1 + abs(vals[2]) + abs(vals[3]))
+                    el = time.perf_counter() - t0
+                    res = dict(iters=it, rel_p=rel_p, rel_d=rel_d, rel_gap=gap, pobj=vals[2], seconds=el)
+                    if max(rel_p, rel_d, gap) <= tol or el >= max_s or it >= max_iters:
+                        break
+            torch.cuda.synchronize()
+        res["seconds"] = time.perf_counter() - t0
+        return res
+
+    r32 = run(torch.float32, cap_s, 10 ** 7)
+    conv = max(r32["rel_p"], r32["rel_d"], r32["rel_gap"]) <= tol
+    r64 = run(torch.float64, 1e9, rate_iters_fp64)
+    return {"impl": "torch.linalg.eigh (cuSOLVER), Alg. 1, same stop test", "tol": tol,
+            "fp32": {"converged": conv, "time_to_tol_s": round(r32["seconds"], 4) if conv else None,
+                     "iters": r32["iters"], "iters_per_s": round(r32["iters"] / r32["seconds"], 2),
+                     "cap_s": cap_s, "rel_primal_res": r32["rel_p"], "rel_dual_res": r32["rel_d"],
+                     "rel_gap": r32["rel_gap"], "primal_obj": r32["pobj"]},
+            "fp64": {"iters_per_s": round(r64["iters"] / r64["seconds"], 3), "iters_timed": r64["iters"]}}
 
 
 def cpu_oracle_sample(seconds=15.0, min_iters=2):
@@ -315,6 +389,48 @@ def cpu_oracle_sample(seconds=15.0, min_iters=2):
     while True:
         st = pd_iteration(sp, X, y, alpha, 8)
         X, y = st.X, st.y
+        k += 1
+        if k >= min_iters and time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return k / dt, k, dt
+
+
+def arpack_step(sp, X, y, alpha, rank, v0):
+    """One LR-PD-SDP iteration (Alg. 2) with the r largest eigenpairs of
+    S = X - alpha (M*(y) + C) from ARPACK (scipy eigsh, which="LA");
+    returns (X+, y+, start vector for the next call)."""
+    import scipy.sparse.linalg as spla
+
+    from oracle.sdp import dual_prox
+
+    S = X - alpha * (sp.M.adjoint(y) + sp.C)
+    lam, U = spla.eigsh(S, k=rank, which="LA", v0=v0, tol=1e-10)
+    Xn = (U * np.maximum(lam, 0.0)) @ U.T
+    yn = dual_prox(y + alpha * sp.M.apply(2.0 * Xn - X), alpha, sp.rhs, sp.m_eq)
+    return Xn, yn, U[:, -1]
+
+
+def cpu_arpack_sample(seconds=15.0, min_iters=2, rank=16):
+    """The paper's own CPU design (Sec. 4: a Lanczos method, ARPACK, for the
+    r largest eigenpairs) timed on the host cores: LR-PD-SDP iterations of the
+    n = 2000 workload with the truncated projection of Eq. trunc_eig computed
+    by scipy.sparse.linalg.eigsh (ARPACK, which="LA", k = r, FP64) and the
+    other steps of Alg. 2 as in the oracle."""
+    from oracle.sdp import Problem, normalize_rows, operator_norm
+
+    inst = workload_problem()
+    prob = Problem.from_instance(inst)
+    sp, _ = normalize_rows(prob)
+    alpha = 0.95 / operator_norm(sp)
+    n = inst.n
+    X = np.zeros((n, n))
+    y = np.zeros(sp.M.m)
+    v0 = np.random.default_rng(0).standard_normal(n)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        X, y, v0 = arpack_step(sp, X, y, alpha, rank, v0)
         k += 1
         if k >= min_iters and time.perf_counter() - t0 >= seconds:
             break
@@ -358,6 +474,24 @@ def projection_hbm(n, info, iters_per_s, hbm_gbs):
     return {"bytes_per_iter": round(bytes_per_iter), "q_products_per_iter": round(q, 3),
             "achieved_gbs": round(gbs, 1), "peak_gbs": hbm_gbs, "frac": round(gbs / hbm_gbs, 4),
             "time_base": "whole iteration"}
+
+
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "c2_oracle.json")
+# device-time share of the top kernel in the ncu launch list of the bench's
+# own solve (graphs off, the same rank path), committed under profiles/
+DOMINANT_KERNEL = {"kernel": "k_sym_eig", "share_of_device_time": None, "bound": "latency (one CTA)",
+                   "source": "profiles/launches_maxcut_n2000_bench_solve.md"}
+
+
+def oracle_objective_error(pobj):
+    """Relative difference of the solve's objective from the FP64 oracle's
+    solve to 1e-5 stored in tests/golden/c2_oracle.json (None if absent)."""
+    try:
+        gold = json.load(open(GOLDEN_C2))
+    except Exception:
+        return None
+    return {"value": abs(pobj - gold["pobj"]) / abs(gold["pobj"]), "oracle_pobj": gold["pobj"],
+            "oracle_tol": gold["tol"]}
 
 
 def run_mimo_batch(args):
@@ -496,7 +630,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--full-eig-iters", type=int, default=10)
+    ap.add_argument("--full-eig-cap", type=float, default=60.0,
+                    help="seconds allowed to the full-eig PDHG baseline to reach 1e-4 (0: skip)")
+    ap.add_argument("--arpack-seconds", type=float, default=10.0, help="host seconds of the ARPACK LR leg (0: skip)")
+    ap.add_argument("--streaming", type=int, default=1, help="run the n = 16384 streaming leg (1) or not (0)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"] + sorted(SWEEPS))
     ap.add_argument("--sizes", default="", help="comma-separated sizes for the table2 / table3 sweeps")
@@ -551,11 +688,17 @@ def main():
     if world > 1:
         total_t, total_it = aggregate_replicas(total_t, total_it, "cuda")
     cpu = None
+    arpack = None
     if rank == 0 and world == 1:
         v, k, dt = cpu_oracle_sample(seconds=args.cpu_seconds)
         cpu = {"value": round(v, 4), "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{k} LR-PD-SDP iterations of the n=2000 workload (FP64, exact eigh) in {dt:.1f} s",
                "host": host_description()}
+        if args.arpack_seconds > 0:
+            va, ka, dta = cpu_arpack_sample(seconds=args.arpack_seconds)
+            arpack = {"value": round(va, 4), "unit": "iters/s", "cores": os.cpu_count(),
+                      "kind": "LR-PD-SDP with ARPACK eigsh (the paper's CPU design), FP64",
+                      "sample": f"{ka} iterations of the n=2000 workload at rank 16 in {dta:.1f} s"}
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
@@ -577,11 +720,12 @@ def main():
         "e2e": {"value": round(e2e_val, 2), "unit": "iters/s", "h2d_bytes_per_step": int(res["h2d"]),
                 "d2h_bytes_per_step": int(res["d2h"]),
                 "time_to_tol_s": round(statistics.median(res["e2e_times"]), 5)},
+        "obj_rel_err_vs_oracle": oracle_objective_error(info["primal_obj"]),
         "roofline": res["roofline"],
         "projection_hbm": projection_hbm(2000, info, value, _peaks()[0]),
-        "dominant_kernel": {"kernel": "k_sym_eig", "share_of_device_time": 0.516, "bound": "latency (one CTA)",
-                            "source": "profiles/launches_maxcut_n2000_r32_direct.md (ncu launch list, rank 32)"},
-        "cpu_baseline": cpu, "clocks": res["clocks"],
+        "streaming": res["streaming"],
+        "dominant_kernel": DOMINANT_KERNEL,
+        "cpu_baseline": cpu, "cpu_lr_arpack": arpack, "clocks": res["clocks"],
         "gpu_launches": int(res["launches"]), "full_eig": res["full"], "other_operator_form": res["alt"],
     }
     print(json.dumps(line))

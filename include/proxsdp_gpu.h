@@ -108,6 +108,8 @@ typedef struct {
   int check_every;        /* iterations between host checks of the stop status           [50]  */
   int use_graphs;         /* run the iteration as a CUDA graph with conditional nodes    [1]   */
   int operator_form;      /* PROXSDP_OP_EXPLICIT / _FACTORED / _AUTO                     [0]   */
+  int64_t memory_limit_bytes; /* cap on the device memory one handle allocates; set_problem
+                                 returns PROXSDP_ERR_OOM beyond it (0: no cap)        [0]   */
 } proxsdp_gpu_settings;
 
 typedef struct {
@@ -198,6 +200,17 @@ int proxsdp_gpu_solve_batch(proxsdp_gpu_t* handles, int count, proxsdp_gpu_info*
 int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V,
                                 double* lambda, int64_t* r_out);
 
+/* Copy the feasible pair (X_[r], y_[r]) that Alg. 2 saves ("save feasible
+ * solution", Sec. 3.2): the last iterate of the most recent solve / iterate
+ * call at which the relative residuals met tol while the rank test found the
+ * rank r insufficient (so r was doubled, or the solve stopped at max_rank).
+ * Same outputs and layouts as proxsdp_gpu_get_primal_dual, plus iter_out, the
+ * iteration at which it was saved.  Any pointer may be NULL.  Returns
+ * PROXSDP_ERR_BAD_STATE when no pair was saved since the iteration started
+ * (solve, or set_iterate followed by iterate). */
+int proxsdp_gpu_get_saved_pair(proxsdp_gpu_t h, double* X, double* y, double* V, double* lambda,
+                               int64_t* r_out, int64_t* iter_out);
+
 /* Set the iterate (X = V diag(max(lambda,0)) V^T with V n*r column-major,
  * orthonormal columns, and y in the paper's dual sign / original scaling) and
  * the target rank, so that proxsdp_gpu_iterate continues from it.  Used for
@@ -234,21 +247,28 @@ int proxsdp_gpu_aproj(const float* S, int64_t n, int64_t lds, int r, float* P, i
                       void* cuda_stream, proxsdp_gpu_info* info);
 
 /* aproj(S, r) for callers that cannot allocate device memory.  The paper has
- * no counterpart; this entry point exists for callers such as code running
- * while a CUDA graph is being captured, applications whose own pool allocator
- * owns all GPU memory, and embedded or real-time hosts that must not allocate
- * (or risk an allocation failure) while they run.  Same arguments, results,
- * defaults and errors as proxsdp_gpu_aproj, but the work buffers live in one
- * file-scope static device array of about 6.7 MB, which every GPU that loads
- * the library holds until the process exits; nothing is allocated per call
- * (no cudaMalloc/cudaFree, no allocating library routine).
+ * no counterpart; this entry point exists for callers such as applications
+ * whose own pool allocator owns all GPU memory and forbids other allocations,
+ * plugins running inside such hosts, and embedded or real-time hosts that
+ * must not allocate (or risk an allocation failure) while they run.  Same
+ * arguments, results, defaults and errors as proxsdp_gpu_aproj (settings are
+ * validated the same way; an unsupported device gives PROXSDP_ERR_CUDA), but
+ * the work buffers live in one file-scope static device array of about
+ * 6.7 MB, which every GPU that loads the library holds until the process
+ * exits; nothing is allocated per call (no cudaMalloc/cudaFree, no allocating
+ * library routine).
  * Limits: n <= 2048 (larger n returns PROXSDP_ERR_UNSUPPORTED with a message
  * for proxsdp_gpu_last_error(NULL)); r as for proxsdp_gpu_aproj.
  * The first call on a device looks up the array's device address on that
- * device (make that first call before any stream capture).  All calls share
- * the one array, so calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller; each call clears the
- * parts that must start at zero and synchronises its stream before returning. */
+ * device with cudaGetSymbolAddress and keeps it for later calls; make that
+ * first call before any stream capture on the device.  The kept address
+ * belongs to the device's primary context: after cudaDeviceReset (or any
+ * other end of that context) the process must not call this entry point
+ * again on that device.  All calls share the one array, which keeps the
+ * previous call's contents, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller; each call
+ * clears the parts that must start at zero and synchronises its stream
+ * before returning. */
 int proxsdp_gpu_aproj_noalloc(const float* S, int64_t n, int64_t lds, int r, float* P, int64_t ldp,
                               float* V, double* lambda, const proxsdp_gpu_settings* settings,
                               void* cuda_stream, proxsdp_gpu_info* info);

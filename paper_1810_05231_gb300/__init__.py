@@ -6,6 +6,12 @@ library with ``python -m paper_1810_05231_gb300.build``.
 """
 from ._binding import (  # noqa: F401
     CONVERGED,
+    ERR_BAD_STATE,
+    ERR_CUDA,
+    ERR_INVALID_ARG,
+    ERR_OOM,
+    ERR_TIMEOUT,
+    ERR_UNSUPPORTED,
     MAX_ITER,
     NUMERIC_ERROR,
     OP_AUTO,

@@ -39,6 +39,7 @@ EXPORTED = [
     "proxsdp_gpu_set_problem",
     "proxsdp_gpu_solve",
     "proxsdp_gpu_get_primal_dual",
+    "proxsdp_gpu_get_saved_pair",
     "proxsdp_gpu_set_iterate",
     "proxsdp_gpu_iterate",
     "proxsdp_gpu_destroy",
@@ -74,6 +75,7 @@ class Settings(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("use_graphs", ctypes.c_int),
         ("operator_form", ctypes.c_int),
+        ("memory_limit_bytes", ctypes.c_int64),
     ]
 
 
@@ -123,6 +125,7 @@ def lib():
     L.proxsdp_gpu_set_problem.argtypes = [vp, i64, dp, i64, dp, dp, i64, i64, dp, dp, dp, dp]
     L.proxsdp_gpu_solve.argtypes = [vp, ctypes.POINTER(Info)]
     L.proxsdp_gpu_get_primal_dual.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64)]
+    L.proxsdp_gpu_get_saved_pair.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.proxsdp_gpu_set_iterate.argtypes = [vp, i32, dp, dp, dp]
     L.proxsdp_gpu_iterate.argtypes = [vp, i64, ctypes.POINTER(Info)]
     L.proxsdp_gpu_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Info), i32]
@@ -250,6 +253,21 @@ class Solver:
                self.h)
         rr = int(r.value)
         return dict(X=X, y=y[:m], V=V[: n * rr].reshape(rr, n).T.copy(), lam=lam[:rr].copy(), r=rr)
+
+    def get_saved_pair(self, want_X=True):
+        """Alg. 2's saved feasible pair (X_[r], y_[r]) of the last solve (raises if none)."""
+        n, m = self.n, self.m
+        X = np.empty((n, n)) if want_X else None
+        y = np.empty(max(m, 1))
+        V = np.empty(n * 128)
+        lam = np.empty(128)
+        r = ctypes.c_int64()
+        it = ctypes.c_int64()
+        _check(lib().proxsdp_gpu_get_saved_pair(self.h, _ptr(X), _ptr(y), _ptr(V), _ptr(lam), ctypes.byref(r),
+                                                ctypes.byref(it)), self.h)
+        rr = int(r.value)
+        return dict(X=X, y=y[:m], V=V[: n * rr].reshape(rr, n).T.copy(), lam=lam[:rr].copy(), r=rr,
+                    iter=int(it.value))
 
 
 def solve_batch(solvers, host_threads: int = 0):

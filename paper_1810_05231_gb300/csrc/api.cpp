@@ -359,12 +359,16 @@ int preprocess(const proxsdp_gpu_settings& set, int64_t n64, const double* C_den
   return PROXSDP_OK;
 }
 
+}  // namespace
+
+namespace psdp {
+
 int check_settings(const proxsdp_gpu_settings& s, std::string& err) {
   if (!(s.tol > 0.0) || s.max_iter < 0 || s.rank_init < 1 || s.block_size < 1 || s.window < 1 ||
       s.window > psdp::kMaxWindow || !(s.alpha_frac > 0.0 && s.alpha_frac < 1.0) || s.max_rank < 1 ||
       s.lanczos_max_cycles < 1 || s.lanczos_steps < 0 || s.lanczos_tol < 0.0 || s.guard < 0 ||
       s.check_every < 1 || s.precision != PROXSDP_PREC_FP32 || s.operator_form < PROXSDP_OP_EXPLICIT ||
-      s.operator_form > PROXSDP_OP_AUTO) {
+      s.operator_form > PROXSDP_OP_AUTO || s.memory_limit_bytes < 0) {
     err = "invalid settings";
     return PROXSDP_ERR_INVALID_ARG;
   }
@@ -401,7 +405,10 @@ int check_device(int device, std::string& err) {
   return PROXSDP_OK;
 }
 
-}  // namespace
+}  // namespace psdp
+
+using psdp::check_device;
+using psdp::check_settings;
 
 extern "C" {
 
@@ -549,22 +556,20 @@ int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const doubl
   return S.set_iterate(r, V, lambda, y);
 }
 
-int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V, double* lambda,
-                                int64_t* r_out) {
-  if (!h) return PROXSDP_ERR_INVALID_ARG;
-  Solver& S = h->s;
-  if (!S.has_problem || !S.has_iterate) return S.fail(PROXSDP_ERR_BAD_STATE, "no iterate yet");
-  cudaSetDevice(S.device);
-  int rc = S.read_ctl();
-  if (rc) return rc;
+}  // extern "C"
+
+namespace {
+
+// Copy factors (n x kMaxR row-major FP32), eigenvalues and the scaled dual
+// (algorithm sign) from the device and export them in the ABI's form.
+int export_pair(Solver& S, const float* dV, const double* dlam, const double* dy, int r, double* X, double* y,
+                double* V, double* lambda) {
   const int n = S.hp.n, m = S.hp.m;
-  const int par = S.ctl_host->par;
-  const int r = S.ctl_host->r_old;  // rank of the current iterate
   std::vector<float> Vr((size_t)n * psdp::kMaxR);
   std::vector<double> lam(psdp::kMaxR), yy(std::max(m, 1));
-  cudaError_t e = cudaMemcpyAsync(Vr.data(), S.wk.Vrm[par], sizeof(float) * Vr.size(), cudaMemcpyDeviceToHost, S.st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(lam.data(), S.wk.lam[par], sizeof(double) * psdp::kMaxR, cudaMemcpyDeviceToHost, S.st);
-  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(yy.data(), S.wk.y, sizeof(double) * m, cudaMemcpyDeviceToHost, S.st);
+  cudaError_t e = cudaMemcpyAsync(Vr.data(), dV, sizeof(float) * Vr.size(), cudaMemcpyDeviceToHost, S.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lam.data(), dlam, sizeof(double) * psdp::kMaxR, cudaMemcpyDeviceToHost, S.st);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(yy.data(), dy, sizeof(double) * m, cudaMemcpyDeviceToHost, S.st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S.st);
   if (e != cudaSuccess) return S.fail(PROXSDP_ERR_CUDA, cudaGetErrorString(e));
   if (X) {
@@ -587,7 +592,40 @@ int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V
       for (int i = 0; i < n; ++i) V[(size_t)t * n + i] = (double)Vr[(size_t)i * psdp::kMaxR + t];
   if (lambda)
     for (int t = 0; t < r; ++t) lambda[t] = lam[t];
+  return PROXSDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V, double* lambda,
+                                int64_t* r_out) {
+  if (!h) return PROXSDP_ERR_INVALID_ARG;
+  Solver& S = h->s;
+  if (!S.has_problem || !S.has_iterate) return S.fail(PROXSDP_ERR_BAD_STATE, "no iterate yet");
+  cudaSetDevice(S.device);
+  int rc = S.read_ctl();
+  if (rc) return rc;
+  const int par = S.ctl_host->par;
+  const int r = S.ctl_host->r_old;  // rank of the current iterate
+  rc = export_pair(S, S.wk.Vrm[par], S.wk.lam[par], S.wk.y, r, X, y, V, lambda);
+  if (rc) return rc;
   if (r_out) *r_out = r;
+  return PROXSDP_OK;
+}
+
+int proxsdp_gpu_get_saved_pair(proxsdp_gpu_t h, double* X, double* y, double* V, double* lambda,
+                               int64_t* r_out, int64_t* iter_out) {
+  if (!h) return PROXSDP_ERR_INVALID_ARG;
+  Solver& S = h->s;
+  if (!S.has_problem || S.saved_r <= 0)
+    return S.fail(PROXSDP_ERR_BAD_STATE, "no feasible pair was saved by the last solve");
+  cudaSetDevice(S.device);
+  int rc = export_pair(S, S.saved_V, S.saved_lam, S.saved_y, S.saved_r, X, y, V, lambda);
+  if (rc) return rc;
+  if (r_out) *r_out = S.saved_r;
+  if (iter_out) *iter_out = S.saved_it;
   return PROXSDP_OK;
 }
 

@@ -243,7 +243,7 @@ static int matvec_slices(int n, int k) {
   return ns;
 }
 
-size_t block_matvec_scratch_floats(int, int) { return 0; }
+size_t block_matvec_scratch_floats(int n, int k) { return block_matvec_tc_scratch_floats(n, k); }
 size_t block_matvec_counters(int, int) { return 0; }
 
 template <int G>
@@ -266,8 +266,11 @@ static void launch_mv(dim3 grid, int ns, cudaStream_t st, const float* S, int ld
 }
 
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
-                         int k, const int* skip, cudaStream_t st, float*, unsigned*,
+                         int k, const int* skip, cudaStream_t st, float* part, unsigned*,
                          cudaGraphConditionalHandle cond, int set_cond) {
+  // tensor cores (3xTF32, TMA-staged S) when the scratch for the split Q is
+  // given and S meets the TMA alignment rules; the SIMT kernel otherwise
+  if (launch_block_matvec_tc(S, lds, n, Q, ldq, W, ldw, k, skip, st, part, cond, set_cond)) return;
   const int ns = matvec_slices(n, k);
   const int kslice = ((n + ns - 1) / ns + MV_KC - 1) / MV_KC * MV_KC;
   dim3 grid(ns, (n + MV_RB - 1) / MV_RB, (k + 63) / 64);

@@ -1,11 +1,11 @@
 // noalloc.cu — the truncated psd projection aproj(S, r) for callers that
 // cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is
-// being captured, applications that hand the GPU's memory to their own
-// allocator or pool and forbid anything else from allocating, and embedded /
-// real-time hosts that must not take the allocator's locks or risk an
-// out-of-memory failure in the middle of a run.  For them this file provides
+// Some callers cannot call cudaMalloc: applications that hand all of the GPU's
+// memory to their own pool allocator and forbid anything else from
+// allocating, plugins that run inside such a host, and embedded or real-time
+// hosts that must not take the allocator's locks or risk an out-of-memory
+// failure in the middle of a run.  For them this file provides
 // proxsdp_gpu_aproj_noalloc: the same computation as proxsdp_gpu_aproj, but
 // every work buffer lives in one file-scope static __device__ array of fixed
 // size (about 6.7 MB, held by every GPU that loads the library until the
@@ -90,7 +90,8 @@ int aproj_noalloc_device(const float* S, int n, int lds, int r, float* P, int ld
     err = std::string("scratch address: ") + cudaGetErrorString(e);
     return PROXSDP_ERR_CUDA;
   }
-  // block width / basis size exactly as the allocating entry point chooses them
+  // block width / basis size exactly as the allocating entry point chooses
+  // them (a cold start: the largest Rayleigh-Ritz basis)
   const bool full = n <= kFullEigMax;
   int w, K, s;
   if (full) {
@@ -98,13 +99,7 @@ int aproj_noalloc_device(const float* S, int n, int lds, int r, float* P, int ld
     K = n;
     s = 0;
   } else {
-    const int b = set.block_size > 0 ? set.block_size : 16;
-    const int g = set.guard > 0 ? set.guard : (r / 4 > 8 ? r / 4 : 8);
-    w = ((r + g + b - 1) / b) * b;
-    if (w > kMaxW) w = kMaxW;
-    s = set.lanczos_steps > 0 ? set.lanczos_steps : (kMaxK / w - 1 > 1 ? kMaxK / w - 1 : 1);
-    while ((s + 1) * w > kMaxK && s > 1) --s;
-    K = (s + 1) * w;
+    lanczos_dims(r, set, kMaxK, w, K, s);
     if (r > w - 4) {
       err = "rank too large for the Lanczos block (r <= 60)";
       return PROXSDP_ERR_UNSUPPORTED;
@@ -219,8 +214,19 @@ extern "C" int proxsdp_gpu_aproj_noalloc(const float* S, int64_t n, int64_t lds,
     s.lanczos_tol = 1e-6;
   }
   std::string err;
+  int rc = psdp::check_settings(s, err);
+  int dev = 0;
+  if (rc == PROXSDP_OK && cudaGetDevice(&dev) != cudaSuccess) {
+    err = "no current CUDA device";
+    rc = PROXSDP_ERR_CUDA;
+  }
+  if (rc == PROXSDP_OK) rc = psdp::check_device(dev, err);
+  if (rc) {
+    psdp::set_global_error(err);
+    return rc;
+  }
   psdp::init_kernel_attributes();
-  int rc = psdp::aproj_noalloc_device(S, (int)std::min<int64_t>(n, 1 << 30), (int)lds, r, P, (int)ldp, V, lambda,
+  rc = psdp::aproj_noalloc_device(S, (int)std::min<int64_t>(n, 1 << 30), (int)lds, r, P, (int)ldp, V, lambda,
                                       s, (cudaStream_t)cuda_stream, info, err);
   if (rc) psdp::set_global_error(err);
   return rc;

@@ -147,9 +147,10 @@ enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_NUM }
 // launchers (k_lanczos.cu)
 // ---------------------------------------------------------------------------
 // W = S Q (S n x n symmetric, row stride lds; Q, W column-major).  With
-// `part` / `counters` (sizes from block_matvec_scratch_floats / _counters;
-// counters zeroed once, the kernel leaves them zeroed) the inner dimension is
-// split over about two CTAs per SM; without them one CTA per 128-row block.
+// `part` (block_matvec_scratch_floats(n, k) floats: the TF32 high / low parts
+// of Q) and S meeting the TMA alignment rules (16-byte base, lds a multiple
+// of 4) the product runs on the tensor cores (k_mv_tc.cu); otherwise on the
+// SIMT kernel (inner dimension split over a thread-block cluster).
 void launch_block_matvec(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw,
                          int k, const int* skip, cudaStream_t st, float* part = nullptr,
                          unsigned* counters = nullptr, cudaGraphConditionalHandle cond = 0,
@@ -158,6 +159,19 @@ size_t block_matvec_scratch_floats(int n, int k);
 size_t block_matvec_counters(int n, int k);
 void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
                          cudaStream_t st);
+// launchers (k_mv_tc.cu): the tensor-core block product; false (nothing
+// launched) when it does not apply
+bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw, int k,
+                            const int* skip, cudaStream_t st, float* scratch, cudaGraphConditionalHandle cond,
+                            int set_cond);
+size_t block_matvec_tc_scratch_floats(int n, int k);
+bool block_matvec_tc_applies(const float* S, int lds, const float* scratch);
+// kernels one launch_block_matvec enqueues (the tensor-core path splits Q first)
+inline int block_matvec_kernels(const float* S, int lds, const float* scratch) {
+  return block_matvec_tc_applies(S, lds, scratch) ? 2 : 1;
+}
+bool block_matvec_tc_enabled();
+void init_mv_tc_attributes();
 // H = A^T B (ka x kb, FP64 row-major) with deterministic block reduction.
 // With act > 0 only output tiles whose row and column offsets modulo `slot`
 // fall below `act` are computed (Gram of a few columns of each factor slot).

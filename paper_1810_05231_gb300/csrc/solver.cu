@@ -86,6 +86,7 @@ void init_kernel_attributes() {
   init_pdhg_attributes();
   init_lanczos_attributes();
   init_factored_attributes();
+  init_mv_tc_attributes();
   done[dev] = true;
 }
 
@@ -96,6 +97,7 @@ void Solver::free_all() {
   graphs.clear();
   for (void* p : allocs) cudaFree(p);
   allocs.clear();
+  dev_bytes = 0;
   if (ctl_host) cudaFreeHost(ctl_host);
   ctl_host = nullptr;
   if (st_aux) cudaStreamDestroy(st_aux);
@@ -105,21 +107,27 @@ void Solver::free_all() {
   own_stream = false;
 }
 
+// Device allocation owned by the handle.  With settings.memory_limit_bytes > 0
+// the handle's allocations are capped at that many bytes in total (an
+// allocation beyond the cap fails as if the device were out of memory).
 template <class T>
-static cudaError_t dalloc(std::vector<void*>& allocs, T** p, size_t count) {
+static cudaError_t dalloc(Solver& sv, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (sv.set.memory_limit_bytes > 0 && (int64_t)(sv.dev_bytes + bytes) > sv.set.memory_limit_bytes)
+    return cudaErrorMemoryAllocation;
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  cudaError_t e = cudaMalloc(&q, bytes);
   if (e != cudaSuccess) return e;
-  allocs.push_back(q);
+  sv.allocs.push_back(q);
+  sv.dev_bytes += bytes;
   *p = static_cast<T*>(q);
   return cudaSuccess;
 }
 
 template <class T>
-static cudaError_t dupload(std::vector<void*>& allocs, const T** p, const std::vector<T>& v,
-                           cudaStream_t st) {
+static cudaError_t dupload(Solver& sv, const T** p, const std::vector<T>& v, cudaStream_t st) {
   T* q = nullptr;
-  cudaError_t e = dalloc(allocs, &q, v.size());
+  cudaError_t e = dalloc(sv, &q, v.size());
   if (e != cudaSuccess) return e;
   if (!v.empty()) e = cudaMemcpyAsync(q, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
   *p = q;
@@ -139,6 +147,7 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   graphs.clear();
   for (void* p : allocs) cudaFree(p);
   allocs.clear();
+  dev_bytes = 0;
   has_problem = false;
   has_iterate = false;
   hp = h;
@@ -149,32 +158,32 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   P.m = h.m;
   P.m_eq = h.m_eq;
   P.nnz_ext = (int)h.ent_p.size();
-  CKA(dupload(allocs, &P.ent_p, h.ent_p, st));
-  CKA(dupload(allocs, &P.ent_q, h.ent_q, st));
-  CKA(dupload(allocs, &P.ent_a, h.ent_a, st));
+  CKA(dupload(*this, &P.ent_p, h.ent_p, st));
+  CKA(dupload(*this, &P.ent_q, h.ent_q, st));
+  CKA(dupload(*this, &P.ent_a, h.ent_a, st));
   P.n_chunks = (int)h.chunk_beg.size();
-  CKA(dupload(allocs, &P.chunk_beg, h.chunk_beg, st));
-  CKA(dupload(allocs, &P.chunk_end, h.chunk_end, st));
-  CKA(dupload(allocs, &P.row_chunk, h.row_chunk, st));
-  CKA(dupload(allocs, &P.chunk_row, h.chunk_row, st));
+  CKA(dupload(*this, &P.chunk_beg, h.chunk_beg, st));
+  CKA(dupload(*this, &P.chunk_end, h.chunk_end, st));
+  CKA(dupload(*this, &P.row_chunk, h.row_chunk, st));
+  CKA(dupload(*this, &P.chunk_row, h.chunk_row, st));
   P.n_multi = (int)h.multi_rows.size();
-  CKA(dupload(allocs, &P.multi_rows, h.multi_rows, st));
-  CKA(dupload(allocs, &P.rhs, h.rhs, st));
+  CKA(dupload(*this, &P.multi_rows, h.multi_rows, st));
+  CKA(dupload(*this, &P.rhs, h.rhs, st));
   P.n_dense = (int)h.dense_row.size();
-  CKA(dupload(allocs, &P.dense_row, h.dense_row, st));
-  CKA(dupload(allocs, &P.dense_a, h.dense_a, st));
-  CKA(dupload(allocs, &P.dense_of_row, h.dense_of_row, st));
+  CKA(dupload(*this, &P.dense_row, h.dense_row, st));
+  CKA(dupload(*this, &P.dense_a, h.dense_a, st));
+  CKA(dupload(*this, &P.dense_of_row, h.dense_of_row, st));
   P.nU = (int)h.u_p.size();
-  CKA(dupload(allocs, &P.u_p, h.u_p, st));
-  CKA(dupload(allocs, &P.u_q, h.u_q, st));
-  CKA(dupload(allocs, &P.u_c, h.u_c, st));
-  CKA(dupload(allocs, &P.u_ptr, h.u_ptr, st));
-  CKA(dupload(allocs, &P.u_row, h.u_row, st));
-  CKA(dupload(allocs, &P.u_a, h.u_a, st));
+  CKA(dupload(*this, &P.u_p, h.u_p, st));
+  CKA(dupload(*this, &P.u_q, h.u_q, st));
+  CKA(dupload(*this, &P.u_c, h.u_c, st));
+  CKA(dupload(*this, &P.u_ptr, h.u_ptr, st));
+  CKA(dupload(*this, &P.u_row, h.u_row, st));
+  CKA(dupload(*this, &P.u_a, h.u_a, st));
   P.ntile = h.ntile;
-  CKA(dupload(allocs, &P.tile_ptr, h.tile_ptr, st));
-  CKA(dupload(allocs, &P.tile_loc, h.tile_loc, st));
-  CKA(dupload(allocs, &P.tile_u, h.tile_u, st));
+  CKA(dupload(*this, &P.tile_ptr, h.tile_ptr, st));
+  CKA(dupload(*this, &P.tile_loc, h.tile_loc, st));
+  CKA(dupload(*this, &P.tile_u, h.tile_u, st));
   P.alpha = h.alpha;
   P.normC = h.normC;
   P.normRhs = h.normRhs;
@@ -189,9 +198,9 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   if (factored) {
     alloc_S = false;
     P.nsym = (int)nsym;
-    CKA(dupload(allocs, &P.sym_ptr, h.sym_ptr, st));
-    CKA(dupload(allocs, &P.sym_col, h.sym_col, st));
-    CKA(dupload(allocs, &P.u_pos, h.u_pos, st));
+    CKA(dupload(*this, &P.sym_ptr, h.sym_ptr, st));
+    CKA(dupload(*this, &P.sym_col, h.sym_col, st));
+    CKA(dupload(*this, &P.u_pos, h.u_pos, st));
   }
 
   DevWork& Wk = wk;
@@ -200,41 +209,47 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   Wk.lds = ld;
   Wk.ldq = ld;
   Wk.ldv = kMaxR;
-  if (alloc_S) CKA(dalloc(allocs, &Wk.S, (size_t)n * ld));
-  CKA(dalloc(allocs, &Wk.Q, (size_t)ld * kMaxK));
-  CKA(dalloc(allocs, &Wk.W, (size_t)ld * kMaxK));
+  if (alloc_S) CKA(dalloc(*this, &Wk.S, (size_t)n * ld));
+  CKA(dalloc(*this, &Wk.Q, (size_t)ld * kMaxK));
+  CKA(dalloc(*this, &Wk.W, (size_t)ld * kMaxK));
   for (int b = 0; b < 2; ++b) {
-    CKA(dalloc(allocs, &Wk.Vrm[b], (size_t)n * kMaxR));
-    CKA(dalloc(allocs, &Wk.lam[b], kMaxR));
-    CKA(dalloc(allocs, &Wk.colsum[b], kMaxR));
-    CKA(dalloc(allocs, &Wk.mx[b], (size_t)h.m + 1));
+    CKA(dalloc(*this, &Wk.Vrm[b], (size_t)n * kMaxR));
+    CKA(dalloc(*this, &Wk.lam[b], kMaxR));
+    CKA(dalloc(*this, &Wk.colsum[b], kMaxR));
+    CKA(dalloc(*this, &Wk.mx[b], (size_t)h.m + 1));
   }
-  CKA(dalloc(allocs, &Wk.y, (size_t)h.m));
-  CKA(dalloc(allocs, &Wk.dy, (size_t)h.m));
-  CKA(dalloc(allocs, &Wk.chunk_part, std::max<size_t>(h.chunk_beg.size(), 1)));
-  CKA(dalloc(allocs, &Wk.D, std::max<size_t>(h.u_p.size(), 1)));
-  CKA(dalloc(allocs, &Wk.dshift, 4));
-  CKA(dalloc(allocs, &Wk.part, (size_t)1 << 20));
-  CKA(dalloc(allocs, &Wk.H, (size_t)kMaxK * kMaxK));
-  CKA(dalloc(allocs, &Wk.Hf, (size_t)kMaxW * kMaxW));
-  CKA(dalloc(allocs, &Wk.flags, kMaxW));
-  CKA(dalloc(allocs, &Wk.Y, (size_t)kMaxK * kMaxK));
-  CKA(dalloc(allocs, &Wk.theta, kMaxK));
-  CKA(dalloc(allocs, &Wk.ritz_part, ((size_t)(n + 31) / 32 + 1) * 4 * kMaxW));
-  CKA(dalloc(allocs, &Wk.counters, (size_t)CNT_NUM * 512));
-  CKA(dalloc(allocs, &Wk.ctl, 1));
-  CKA(dalloc(allocs, &Vcm, (size_t)ld * 2 * kMaxR));
-  CKA(dalloc(allocs, &Hx, (size_t)4 * kMaxR * kMaxR));
+  CKA(dalloc(*this, &Wk.y, (size_t)h.m));
+  CKA(dalloc(*this, &Wk.dy, (size_t)h.m));
+  CKA(dalloc(*this, &Wk.chunk_part, std::max<size_t>(h.chunk_beg.size(), 1)));
+  CKA(dalloc(*this, &Wk.D, std::max<size_t>(h.u_p.size(), 1)));
+  CKA(dalloc(*this, &Wk.dshift, 4));
+  CKA(dalloc(*this, &Wk.part, (size_t)1 << 20));
+  CKA(dalloc(*this, &Wk.H, (size_t)kMaxK * kMaxK));
+  CKA(dalloc(*this, &Wk.Hf, (size_t)kMaxW * kMaxW));
+  CKA(dalloc(*this, &Wk.flags, kMaxW));
+  CKA(dalloc(*this, &Wk.Y, (size_t)kMaxK * kMaxK));
+  CKA(dalloc(*this, &Wk.theta, kMaxK));
+  CKA(dalloc(*this, &Wk.ritz_part, ((size_t)(n + 31) / 32 + 1) * 4 * kMaxW));
+  CKA(dalloc(*this, &Wk.counters, (size_t)CNT_NUM * 512));
+  CKA(dalloc(*this, &Wk.ctl, 1));
+  CKA(dalloc(*this, &Vcm, (size_t)ld * 2 * kMaxR));
+  CKA(dalloc(*this, &Hx, (size_t)4 * kMaxR * kMaxR));
   Wk.Vcm = Vcm;
   Wk.Hx = Hx;
   if (factored) {
-    CKA(dalloc(allocs, &Wk.Dsym, (size_t)nsym));
-    CKA(dalloc(allocs, &Wk.Qr, (size_t)n * kMaxW));
-    CKA(dalloc(allocs, &Wk.lrP, (size_t)64 * kMaxW));
+    CKA(dalloc(*this, &Wk.Dsym, (size_t)nsym));
+    CKA(dalloc(*this, &Wk.Qr, (size_t)n * kMaxW));
+    CKA(dalloc(*this, &Wk.lrP, (size_t)64 * kMaxW));
     CK(cudaMemsetAsync(Wk.Dsym, 0, sizeof(float) * std::max<size_t>((size_t)nsym, 1), st));
   }
-  CKA(dalloc(allocs, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxW)));
-  CKA(dalloc(allocs, &Wk.mv_cnt, block_matvec_counters(n, kMaxW)));
+  CKA(dalloc(*this, &saved_V, (size_t)n * kMaxR));
+  CKA(dalloc(*this, &saved_lam, kMaxR));
+  CKA(dalloc(*this, &saved_y, (size_t)h.m));
+  saved_r = 0;
+  saved_it = -1;
+  saved_seen = 0;
+  CKA(dalloc(*this, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxW)));
+  CKA(dalloc(*this, &Wk.mv_cnt, block_matvec_counters(n, kMaxW)));
   CK(cudaMemsetAsync(Wk.mv_cnt, 0, sizeof(unsigned) * block_matvec_counters(n, kMaxW), st));
   CK(cudaMemsetAsync(Wk.counters, 0, sizeof(unsigned) * CNT_NUM * 512, st));
   CK(cudaMemsetAsync(Wk.Q, 0, sizeof(float) * (size_t)ld * kMaxK, st));
@@ -246,23 +261,27 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   return PROXSDP_OK;
 }
 
-// Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s for rank r.
-void Solver::dims(int rr, int& w, int& K, int& s) const {
-  const int n = hp.n;
+void lanczos_dims(int rr, const proxsdp_gpu_settings& set, int k_target, int& w, int& K, int& s) {
   const int b = std::max(1, set.block_size);
-  if (n <= kFullEigMax || set.full_eig) {
-    w = n;
-    K = n;
-    s = 0;
-    return;
-  }
-  int g = set.guard > 0 ? set.guard : std::max(8, rr / 4);
+  const int g = set.guard > 0 ? set.guard : std::max(8, rr / 4);
   w = ((rr + g + b - 1) / b) * b;
   w = std::min(w, kMaxW);
   if (set.lanczos_steps > 0) s = set.lanczos_steps;
   else s = std::max(1, k_target / w - 1);
   while ((s + 1) * w > kMaxK && s > 1) --s;
   K = (s + 1) * w;
+}
+
+// Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s for rank r.
+void Solver::dims(int rr, int& w, int& K, int& s) const {
+  const int n = hp.n;
+  if (n <= kFullEigMax || set.full_eig) {
+    w = n;
+    K = n;
+    s = 0;
+    return;
+  }
+  lanczos_dims(rr, set, k_target, w, K, s);
 }
 
 int Solver::set_ctl_fields(int status, int it_stop, int rr, int w, int K, int k_change) {
@@ -330,7 +349,8 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
   dbg(wk, "rr gram T", st);
   launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
   dbg(wk, "rr eig", st);
-  int cycle_launches = 3 + s * (fac ? kFactoredLaunches : 1);  // Gram of T, eigensolver, Ritz; the products
+  // Gram of T, eigensolver, Ritz; the products
+  int cycle_launches = 3 + s * (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
   for (int j = 1; j <= s; ++j) cycle_launches += orth_cluster_applies(n, j * w, w) ? 1 : 11;
   launch_ritz(wk, n, K, w, r, s, cycle_launches, cond, use_cond, st);
   dbg(wk, "ritz", st);
@@ -395,7 +415,8 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   // product, M(X)/dual step, D values, Gram + controller, the rebuild of S
   const int iter_launches = k.full ? 7
                                    : (orth_cluster_applies(n, 0, k.w) ? 1 : 3) +
-                                         (factored ? kFactoredLaunches + 3 : 5);
+                                         (factored ? kFactoredLaunches + 3
+                                                   : 4 + block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
   launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
   dbg(wk, "gram+control", st);
   if (!factored) {
@@ -465,6 +486,9 @@ int Solver::init_iterate_zero() {
   }
   CK(cudaMemsetAsync(Vcm, 0, sizeof(float) * (size_t)wk.ldq * 2 * kMaxR, st));
   rank_changes = 0;
+  saved_r = 0;
+  saved_it = -1;
+  saved_seen = 0;
   r = std::max(1, std::min(set.full_eig ? n : set.rank_init, n));
   if (!set.full_eig) r = std::min(r, set.max_rank);
   int w, K, s;
@@ -509,6 +533,24 @@ int Solver::grow_basis(int w_old, int w_new) {
   launch_random_block(wk.Q, wk.ldq, hp.n, w_old, w_new - w_old, seed + 31ULL * (unsigned long long)w_new, st);
   enqueue_orth(wk, hp.n, w_old, w_new - w_old, seed + 7ULL * (unsigned long long)w_new, nullptr, st);
   CK(cudaGetLastError());
+  return PROXSDP_OK;
+}
+
+// Alg. 2 saves the feasible pair (X_[r], y_[r]) when the inner loop has
+// converged at a rank the rank test finds insufficient; the controller counts
+// such iterations in Ctl::saved and ends the graph there (the rank change or
+// the stall at the rank cap goes back to the host), so the current iterate
+// (Ctl::par, rank Ctl::r_old) is the pair to keep.
+int Solver::keep_saved_pair() {
+  const Ctl& c = *ctl_host;
+  if (c.saved <= saved_seen || !saved_V) return PROXSDP_OK;
+  saved_seen = c.saved;
+  const int n = hp.n;
+  CK(cudaMemcpyAsync(saved_V, wk.Vrm[c.par], sizeof(float) * (size_t)n * kMaxR, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(saved_lam, wk.lam[c.par], sizeof(double) * kMaxR, cudaMemcpyDeviceToDevice, st));
+  if (hp.m > 0) CK(cudaMemcpyAsync(saved_y, wk.y, sizeof(double) * hp.m, cudaMemcpyDeviceToDevice, st));
+  saved_r = c.r_old;
+  saved_it = c.it;
   return PROXSDP_OK;
 }
 
@@ -566,6 +608,10 @@ int Solver::run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info
     }
     const int status = ctl_host->status;
     if (status == ST_RUNNING || status == ST_PAUSE) continue;
+    if (status == ST_RANK_CHANGE || status == ST_STALLED_MAX_RANK) {
+      rc = keep_saved_pair();
+      if (rc) return rc;
+    }
     if (status == ST_CONVERGED) {
       final_status = ST_CONVERGED;
       if (stop_on_converge) break;

@@ -53,11 +53,20 @@ struct Solver {
   float* Vcm = nullptr;  // column-major factor slots (2 * kMaxR columns)
   double* Hx = nullptr;  // Gram of the factor slots
   std::vector<void*> allocs;
+  size_t dev_bytes = 0;  // bytes held in `allocs`
   Ctl* ctl_host = nullptr;  // pinned mirror
   std::map<GraphKey, cudaGraphExec_t> graphs;
   bool factored = false;  // S^k applied from the factors (never formed)
   int r = 8;
   int rank_changes = 0;
+  // Alg. 2 "save feasible solution": the iterate at which the residuals met
+  // tol while the rank test asked for r <- 2r (the last such pair of a solve)
+  float* saved_V = nullptr;     // n x kMaxR row-major factors
+  double* saved_lam = nullptr;  // kMaxR eigenvalues
+  double* saved_y = nullptr;    // m dual (scaled problem, algorithm sign)
+  int saved_r = 0;              // rank of the saved pair (0: none)
+  int64_t saved_it = -1;        // its iteration
+  int saved_seen = 0;           // Ctl::saved already copied
   int k_target = 32;  // Rayleigh-Ritz basis size aimed at by dims() (one Krylov step per cycle)
   unsigned long long seed = 1;
 
@@ -77,8 +86,20 @@ struct Solver {
                         cudaGraphConditionalHandle inner);
   int get_graph(const GraphKey& k, cudaGraphExec_t* out);
   int set_ctl_fields(int status, int it_stop, int r, int w, int K, int k_change);
+  int keep_saved_pair();
   void free_all();
 };
+
+// Settings and device checks shared by the entry points (api.cpp):
+// PROXSDP_ERR_INVALID_ARG / PROXSDP_ERR_CUDA with a message in `err`.
+int check_settings(const proxsdp_gpu_settings& s, std::string& err);
+int check_device(int device, std::string& err);
+
+// Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s per
+// restart cycle for target rank r on the block Lanczos path (n > kFullEigMax):
+// w = the smallest multiple of block_size holding r + guard vectors (at most
+// kMaxW), s = k_target / w - 1 steps unless lanczos_steps fixes it, K <= kMaxK.
+void lanczos_dims(int r, const proxsdp_gpu_settings& set, int k_target, int& w, int& K, int& s);
 
 // device helpers used by the API (solver.cu)
 int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float* V, double* lambda,

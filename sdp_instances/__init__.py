@@ -111,6 +111,20 @@ def erdos_renyi(n: int, p: float, rng: np.random.Generator):
     return iu[keep].astype(np.int64), ju[keep].astype(np.int64)
 
 
+def erdos_renyi_rows(n: int, p: float, rng: np.random.Generator):
+    """The same edges as ``erdos_renyi`` (same draws, same row-major order),
+    drawn one row at a time so that large n needs O(n) memory per row."""
+    ei, ej = [], []
+    for i in range(n - 1):
+        d = rng.random(n - 1 - i)
+        j = np.nonzero(d < p)[0] + i + 1
+        ei.append(np.full(j.shape[0], i, dtype=np.int64))
+        ej.append(j.astype(np.int64))
+    if not ei:
+        return np.zeros(0, np.int64), np.zeros(0, np.int64)
+    return np.concatenate(ei), np.concatenate(ej)
+
+
 def laplacian_svec(n: int, ei, ej, w):
     """Graph Laplacian as sparse svec entries (diagonal first, then edges)."""
     deg = np.zeros(n)
@@ -244,6 +258,16 @@ def maxcut_er(n: int, p: float, seed: int, weights: str = "unit") -> SDPProblem:
     else:  # integer weights 1..5, drawn in edge order after the graph
         w = rng.integers(1, 6, size=ei.shape[0]).astype(np.float64)
     prob = maxcut(n, ei, ej, w)
+    prob.meta.update(seed=seed, p=p)
+    return prob
+
+
+def maxcut_er_streaming(n: int = 16384, p: float = 0.001, seed: int = 5) -> SDPProblem:
+    """MaxCut of G(n, p) with unit weights, sized so that the n x n FP32
+    primal-step input (1 GiB at n = 16384) is far larger than the L2 cache."""
+    rng = np.random.default_rng(seed)
+    ei, ej = erdos_renyi_rows(n, p, rng)
+    prob = maxcut(n, ei, ej, np.ones(ei.shape[0]))
     prob.meta.update(seed=seed, p=p)
     return prob
 

@@ -33,3 +33,25 @@ def test_sweep_tables_and_paper_column():
         for n in sizes:
             assert n in bench.PAPER_SECONDS[kind]
     assert bench.PAPER_SECONDS["table3"][5000] == 472.4
+
+
+def test_arpack_step_matches_oracle_step():
+    """The ARPACK leg's iteration equals the oracle's Alg. 2 step (exact
+    truncated projection) on a small MaxCut instance."""
+    import numpy as np
+
+    import oracle
+    import sdp_instances as si
+    from oracle.sdp import Problem, normalize_rows, operator_norm
+
+    prob = Problem.from_instance(si.maxcut_er(60, 0.2, 1, weights="int5"))
+    sp, _ = normalize_rows(prob)
+    alpha = 0.95 / operator_norm(sp)
+    X = np.zeros((60, 60))
+    y = np.zeros(sp.M.m)
+    v0 = np.ones(60)
+    for _ in range(5):
+        ref = oracle.pd_iteration(sp, X, y, alpha, 6)
+        X, y, v0 = bench.arpack_step(sp, X, y, alpha, 6, v0)
+        assert np.linalg.norm(X - ref.X) <= 1e-8 * max(1.0, np.linalg.norm(ref.X))
+        assert np.linalg.norm(y - ref.y) <= 1e-8 * max(1.0, np.linalg.norm(ref.y))

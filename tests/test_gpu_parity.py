@@ -10,8 +10,11 @@ Tolerances (float comparisons):
   relative, residuals within 1e-3 relative (they are differences of nearby
   iterates);
 * converged solves: objective within 1e-4 relative of the closed form or of
-  the oracle.
+  the oracle, certificates (primal infeasibility, relative gap, dual
+  infeasibility) within 1e-4.
 """
+import json
+import os
 import math
 
 import numpy as np
@@ -45,8 +48,11 @@ DEV = "cuda:0"
 # building blocks
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,k", [(1, 1), (17, 3), (300, 16), (1000, 48), (2000, 16), (2049, 7)])
+@pytest.mark.parametrize("n,k", [(1, 1), (17, 3), (300, 16), (1000, 48), (2000, 16), (2049, 7), (2000, 80),
+                                 (2000, 128), (1536, 256), (1537, 130), (5000, 64), (16384, 48), (100, 40)])
 def test_block_matvec(pkg, n, k):
+    """n a multiple of 4 takes the tensor-core kernel (TMA needs 16-byte row
+    strides), other n the SIMT kernel."""
     rng = np.random.default_rng(n + k)
     A = rng.standard_normal((n, n))
     S = (A + A.T) / 2
@@ -85,7 +91,8 @@ def _spectrum(n, npos, seed, gap=0.3):
 
 
 @pytest.mark.parametrize("n,r,npos", [(50, 5, 10), (127, 8, 8), (129, 8, 20), (300, 8, 30), (777, 16, 24),
-                                      (1000, 32, 40), (2000, 8, 12), (2000, 16, 64)])
+                                      (1000, 32, 40), (2000, 8, 12), (2000, 16, 64), (2000, 60, 70),
+                                      (5000, 16, 24)])
 def test_aproj_known_spectrum(pkg, n, r, npos):
     lam = _spectrum(n, npos, seed=n + r)
     # separate lambda_r from lambda_{r+1} by a relative gap so the truncation is unique
@@ -122,7 +129,8 @@ def _shared_iterate(inst, r, iters):
 
 
 @pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
-@pytest.mark.parametrize("kind,n,r", [("maxcut", 200, 4), ("maxcut", 90, 6), ("equi", 160, 8), ("sensor", 0, 8)])
+@pytest.mark.parametrize("kind,n,r", [("maxcut", 200, 4), ("maxcut", 90, 6), ("equi", 160, 8), ("sensor", 0, 8),
+                                      ("workload", 2000, 16)])
 def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
     """form 1 applies S^k from the factors of X^k (n > 128; n = 90 takes the
     dense eigensolver, which always forms S)."""
@@ -132,6 +140,8 @@ def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
         rng = np.random.default_rng(7)
         ei, ej = si.erdos_renyi(n, 0.05, rng)
         inst = si.equipartition(n, ei, ej, np.ones(ei.shape[0]))
+    elif kind == "workload":  # the n = 2000 MaxCut workload (weights 1..5, seed 1)
+        inst = si.config_maxcut_2000()
     else:
         inst = si.sensor_network(140, 6, 0.3, seed=5)
     prob, Vx, lx, yp = _shared_iterate(inst, r, 25)
@@ -158,11 +168,16 @@ def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
 # full solves
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n,graph", [(5, "K"), (6, "K"), (7, "C"), (64, "C"), (16, "K"), (100, "K")])
-def test_maxcut_closed_forms_small(pkg, n, graph):
+@pytest.mark.parametrize("n,graph,tol", [(5, "K", 1e-6), (6, "K", 1e-6), (7, "C", 1e-6), (64, "C", 1e-6),
+                                         (16, "K", 1e-6), (100, "K", 1e-6), (101, "C", 5e-5)])
+def test_maxcut_closed_forms_small(pkg, n, graph, tol):
+    """Dense projection path (n <= 128).  The 101-cycle converges slowly under
+    PDHG (the FP64 oracle needs 35 649 iterations to 1e-4 and 164 457 to
+    1e-5), so it runs at 5e-5: a relative gap tol bounds the objective error
+    by about 2 tol (reading A21)."""
     ei, ej, w = si.complete_graph(n) if graph == "K" else si.cycle_graph(n)
     inst = si.maxcut(n, ei, ej, w)
-    slv = pkg.Solver(tol=1e-6, rank_init=1, max_iter=100000)
+    slv = pkg.Solver(tol=tol, rank_init=1, max_iter=400000)
     slv.set_instance(inst)
     info = slv.solve()
     if graph == "K":
@@ -171,6 +186,42 @@ def test_maxcut_closed_forms_small(pkg, n, graph):
         want = -(n / 2.0) * (1 + math.cos(math.pi / n)) if n % 2 else -float(n)
     assert info.status == pkg.CONVERGED, info.as_dict()
     assert abs(info.primal_obj - want) <= 1e-4 * abs(want)
+    slv.close()
+
+
+@pytest.mark.parametrize("n", [201])
+def test_maxcut_cycle_closed_form_lanczos_path(pkg, n):
+    """An odd cycle with n > 128 (block Krylov path): the MaxCut SDR (Sec. 1.4)
+    of C_n has the value -(n/2)(1 + cos(pi/n)) for odd n.  Solved to 5e-5 so
+    that the objective is within 1e-4 (reading A21)."""
+    ei, ej, w = si.cycle_graph(n)
+    inst = si.maxcut(n, ei, ej, w)
+    slv = pkg.Solver(tol=5e-5, rank_init=2, max_iter=400000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    want = -(n / 2.0) * (1 + math.cos(math.pi / n)) if n % 2 else -float(n)
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - want) <= 1e-4 * abs(want), (info.primal_obj, want)
+    slv.close()
+
+
+def test_c1_full_projection_against_oracle(pkg):
+    """PD-SDP (Alg. 1, exact projection every iteration) on the n = 100
+    MaxCut instance (G(100, 0.1), seed 0) against the oracle's Alg. 1 at a
+    tolerance ten times tighter, with the certificates of the GPU pair."""
+    inst = si.config_maxcut_small()
+    prob = Problem.from_instance(inst)
+    ref = oracle.solve(prob, mode="full", tol=1e-7)
+    assert ref.status == 0
+    slv = pkg.Solver(tol=1e-6, full_eig=1, max_iter=200000)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - ref.pobj) <= 1e-4 * abs(ref.pobj), (info.primal_obj, ref.pobj)
+    got = slv.get_primal_dual()
+    cert = oracle.certificates(prob, got["X"], -got["y"])
+    assert cert["primal_eq"] <= 1e-4 and cert["rel_gap"] <= 1e-4 and cert["dual_min_eig_rel"] >= -1e-4, cert
+    assert cert["x_min_eig_rel"] >= -1e-6
     slv.close()
 
 
@@ -224,15 +275,17 @@ def test_equipartition_dense_row(pkg, form):
     ei, ej = si.erdos_renyi(n, 0.06, rng)
     inst = si.equipartition(n, ei, ej, np.ones(ei.shape[0]))
     prob = Problem.from_instance(inst)
-    # equipartition converges slowly under PDHG: both sides stop at the 1e-4
-    # residual and gap target, so each objective is within ~1e-4 of the optimum
+    # PDHG stalls on this instance above 1e-5 (the FP64 oracle is still at a
+    # relative gap of 3.4e-5 after 100 000 iterations), so both sides stop at
+    # 1e-4; each objective is then within about 2e-4 of the optimum, and so of
+    # each other (reading A21).  The certificates below hold at 1e-4.
     ref = oracle.solve(prob, mode="lr", tol=1e-4, rank_init=16, max_iter=20000)
     assert ref.status == 0  # converged
     slv = pkg.Solver(tol=1e-4, rank_init=16, max_iter=100000, operator_form=form)
     slv.set_instance(inst)
     info = slv.solve()
     assert info.status == pkg.CONVERGED, info.as_dict()
-    assert abs(info.primal_obj - ref.pobj) <= 2e-4 * abs(ref.pobj)
+    assert abs(info.primal_obj - ref.pobj) <= 2e-4 * abs(ref.pobj), (info.primal_obj, ref.pobj)
     got = slv.get_primal_dual()
     # certificates on the row-scaled problem the iteration runs on (reading A6):
     # the dense row 11^T has ||A_i||_F = n, so its residual in the original
@@ -292,18 +345,18 @@ def test_mimo_box_rows_lanczos_path(pkg):
     res = {}
     for box in (False, True):
         inst = si.mimo(150, np.random.default_rng(8), box=box)
-        slv = pkg.Solver(tol=1e-4, rank_init=2, max_iter=400000)
+        slv = pkg.Solver(tol=1e-5, rank_init=2, max_iter=400000)
         slv.set_instance(inst)
         info = slv.solve()
         assert info.status == pkg.CONVERGED, (box, info.as_dict())
         res[box] = (info, slv.get_primal_dual(), inst)
         slv.close()
     p0, p1 = res[False][0].primal_obj, res[True][0].primal_obj
-    assert abs(p1 - p0) <= 3e-4 * (1 + abs(p0)), (p0, p1)
+    assert abs(p1 - p0) <= 1e-4 * (1 + abs(p0)), (p0, p1)
     info, got, inst = res[True]
     assert np.all(got["y"][inst.m_eq:] <= 1e-12)
     cert = oracle.certificates(Problem.from_instance(inst), got["X"], -got["y"])
-    assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 2e-4, cert
+    assert cert["primal_ineq"] <= 1e-4 and cert["rel_gap"] <= 1e-4, cert
 
 
 def test_sensor_positions_small(pkg):
@@ -344,20 +397,44 @@ def test_sensor_positions_lanczos_path(pkg):
 # the n = 2000 MaxCut workload (weights 1..5), certified at full size
 # ---------------------------------------------------------------------------
 
+GOLDEN_C2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_oracle.json")
+
+
 @pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
-def test_maxcut_2000_certified(pkg, form):
+def test_maxcut_2000_objective_against_stored_oracle(pkg, form):
+    """The bench workload as the bench runs it (tol 1e-4): objective within
+    1e-4 relative of the FP64 oracle's solve to 1e-5 (``golden/c2_oracle.json``,
+    written by ``golden/make_c2_oracle.py`` from ``oracle/`` alone)."""
+    gold = json.load(open(GOLDEN_C2))
+    assert gold["status"] == 0 and gold["tol"] <= 1e-5
     inst = si.config_maxcut_2000()
     slv = pkg.Solver(tol=1e-4, rank_init=8, block_size=16, operator_form=form)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert abs(info.primal_obj - gold["pobj"]) <= 1e-4 * abs(gold["pobj"]), (info.primal_obj, gold["pobj"])
+    assert info.rel_gap <= 1e-4
+    slv.close()
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
+def test_maxcut_2000_certified(pkg, form):
+    """Run to 1e-5, the GPU pair certifies the optimum to 1e-4: primal
+    feasibility, relative gap and dual feasibility (lambda_min(C + M*(y)))."""
+    inst = si.config_maxcut_2000()
+    slv = pkg.Solver(tol=1e-5, rank_init=8, block_size=16, operator_form=form)
     slv.set_instance(inst)
     info = slv.solve()
     assert info.status == pkg.CONVERGED, info.as_dict()
     got = slv.get_primal_dual()
     prob = Problem.from_instance(inst)
     cert = oracle.certificates(prob, got["X"], -got["y"])
-    assert cert["primal_eq"] <= 1e-4
-    assert cert["rel_gap"] <= 2e-4
-    assert cert["dual_min_eig_rel"] >= -1e-3
-    assert cert["x_min_eig_rel"] >= -1e-6
+    assert cert["primal_eq"] <= 1e-4, cert
+    assert cert["rel_gap"] <= 1e-4, cert
+    assert cert["dual_min_eig_rel"] >= -1e-4, cert
+    assert cert["x_min_eig_rel"] >= -1e-6, cert
+    gold = json.load(open(GOLDEN_C2))
+    assert abs(cert["pobj"] - gold["pobj"]) <= 1e-4 * abs(gold["pobj"])
     slv.close()
 
 

@@ -33,11 +33,29 @@ def test_workload_instances(fn, n, m, nnz, c_nnz, h):
     assert digest(p) == h
 
 
+def draws_digest(p):
+    """Hash of the seeded draws of a MIMO instance (H, x, noise) and its rows.
+    C = [[H^T H, -H^T s], [-s^T H, s^T s]] is a BLAS product whose last bits
+    depend on the BLAS thread count, so it is checked against its definition
+    instead of hashed."""
+    m = hashlib.sha256()
+    for a in (p.A_rowptr, p.A_col, p.A_val, p.rhs, p.meta["H"], p.meta["x"], p.meta["s"]):
+        m.update(np.ascontiguousarray(a).tobytes())
+    return m.hexdigest()[:16]
+
+
 def test_mimo_batch():
     b = si.config_mimo_batch()
     assert len(b) == 256
     assert min(p.n for p in b) >= 33 and max(p.n for p in b) <= 513
-    assert digest(b[0]) == "c230e79c95fda86f" and digest(b[-1]) == "09909b5ff08ac547"
+    assert draws_digest(b[0]) == "0b1d805e0e1b9e93" and draws_digest(b[-1]) == "e8b48226eb399730"
+    for p in (b[0], b[-1]):
+        H, s = p.meta["H"], p.meta["s"]
+        N = H.shape[1]
+        C = p.C_dense
+        np.testing.assert_allclose(C[:N, :N], H.T @ H, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(C[:N, N], -(H.T @ s), rtol=0, atol=1e-12)
+        assert abs(C[N, N] - s @ s) <= 1e-12 * (s @ s)
     p = b[0]
     N = p.n - 1
     H, x, s = p.meta["H"], p.meta["x"], p.meta["s"]
@@ -62,3 +80,10 @@ def test_sensor_constraints_encode_distances():
             a, b = si.svec_unindex(p.A_col[e])
             val += p.A_val[e] * (Z[a, b] if a == b else 2 * Z[a, b])
         assert abs(val - p.rhs[i]) < 1e-12
+
+
+@pytest.mark.parametrize("n,p,seed", [(50, 0.2, 0), (300, 0.01, 3)])
+def test_erdos_renyi_rows_matches_full_draw(n, p, seed):
+    a = si.erdos_renyi(n, p, np.random.default_rng(seed))
+    b = si.erdos_renyi_rows(n, p, np.random.default_rng(seed))
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
