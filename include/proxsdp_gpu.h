@@ -273,9 +273,15 @@ int proxsdp_gpu_aproj_noalloc(const float* S, int64_t n, int64_t lds, int r, flo
                               float* V, double* lambda, const proxsdp_gpu_settings* settings,
                               void* cuda_stream, proxsdp_gpu_info* info);
 
-/* Symmetric block product W = S * Q (the Lanczos matvec): S n x n FP32 with
- * row stride lds, Q n x k FP32 column-major (stride ldq >= n), W likewise
- * (stride ldw).  k <= 256. */
+/* Symmetric block product W = S * Q (the Lanczos matvec of Sec. 3.1): S
+ * n x n FP32 with row stride lds, Q n x k FP32 column-major (stride
+ * ldq >= n), W likewise (stride ldw).  k <= 256.  When S starts on a 16-byte
+ * boundary and lds is a multiple of 4 the product runs on the tensor cores
+ * (S streamed by TMA, 3xTF32 with FP32 sums, FP32-grade accuracy); otherwise
+ * on the SIMT FP32 kernel.  Scratch (2 * ceil(n/32)*32 * k floats for the
+ * TF32 parts of Q) comes from a library-owned stream-ordered pool that keeps
+ * its largest block until the process exits.  Asynchronous on cuda_stream;
+ * a tensor-core CTA whose bounded waits run out writes NaN to its rows of W. */
 int proxsdp_gpu_block_matvec(const float* S, int64_t n, int64_t lds, const float* Q, int64_t ldq,
                              int k, float* W, int64_t ldw, void* cuda_stream);
 

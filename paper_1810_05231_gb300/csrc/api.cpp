@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -410,6 +411,34 @@ int check_device(int device, std::string& err) {
 using psdp::check_device;
 using psdp::check_settings;
 
+namespace {
+
+// Stream-ordered scratch of the device-pointer entry points comes from a
+// library-owned memory pool per device whose release threshold keeps freed
+// blocks mapped (the default pool unmaps them at every synchronisation, and
+// mapping device memory again costs about 0.1 ms per call).  The pool keeps
+// the largest scratch in use so far until the process exits.
+cudaMemPool_t scratch_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[256] = {};
+  if (dev < 0 || dev >= 256) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+}  // namespace
+
 extern "C" {
 
 int proxsdp_gpu_settings_default(proxsdp_gpu_settings* s) {
@@ -710,21 +739,24 @@ int proxsdp_gpu_block_matvec(const float* S, int64_t n, int64_t lds, const float
   if (cudaGetDevice(&dev) != cudaSuccess) return PROXSDP_ERR_CUDA;
   int rc = check_device(dev, err);
   if (rc) return rc;
+  psdp::init_kernel_attributes();
   cudaStream_t st = (cudaStream_t)cuda_stream;
   float* part = nullptr;
-  unsigned* cnt = nullptr;
-  const size_t np = psdp::block_matvec_scratch_floats((int)n, k), nc = psdp::block_matvec_counters((int)n, k);
-  if (cudaMallocAsync((void**)&part, np * sizeof(float), st) != cudaSuccess ||
-      cudaMallocAsync((void**)&cnt, nc * sizeof(unsigned), st) != cudaSuccess) {
-    if (part) cudaFreeAsync(part, st);
+  const size_t np = psdp::block_matvec_scratch_floats((int)n, k);
+  cudaMemPool_t pool = scratch_pool(dev);
+  if (!pool) return PROXSDP_ERR_CUDA;
+  if (cudaMallocFromPoolAsync((void**)&part, np * sizeof(float), pool, st) != cudaSuccess) {
+    cudaGetLastError();
     return PROXSDP_ERR_OOM;
   }
-  cudaMemsetAsync(cnt, 0, nc * sizeof(unsigned), st);
-  psdp::launch_block_matvec(S, (int)lds, (int)n, Q, (int)ldq, W, (int)ldw, k, nullptr, st, part, cnt);
+  psdp::launch_block_matvec(S, (int)lds, (int)n, Q, (int)ldq, W, (int)ldw, k, nullptr, st, part, nullptr);
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(part, st);
-  cudaFreeAsync(cnt, st);
-  return e == cudaSuccess ? PROXSDP_OK : PROXSDP_ERR_CUDA;
+  if (e != cudaSuccess) {
+    psdp::set_global_error(std::string("block product launch: ") + cudaGetErrorString(e));
+    return PROXSDP_ERR_CUDA;
+  }
+  return PROXSDP_OK;
 }
 
 int proxsdp_gpu_sym_eig(const double* T, int K, double* theta, float* Y, void* cuda_stream) {

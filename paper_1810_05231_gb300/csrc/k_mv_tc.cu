@@ -2,19 +2,30 @@
 // (Sec. 3.1, Eq. trunc_eig) on the fifth-generation tensor cores.
 //
 // S (n x n FP32, symmetric, row stride lds) is streamed from HBM once per
-// product by TMA in 128-row x 32-column tiles (128-byte swizzle); Q (n x k)
-// is split once per product into TF32 high and low parts (hi = Q with the low
-// 13 mantissa bits cleared, lo = Q - hi, both exact in FP32) and streamed by
-// TMA too.  Each CTA owns 128 rows of S and up to 64 columns of Q over one
-// slice of the inner dimension.  Its four warps read their rows of each S
-// tile from shared memory, split them the same way and store S_hi and S_lo
-// into tensor memory (TMEM), and one thread issues
-//     D += S_lo Q_hi + S_hi Q_lo + S_hi Q_hi
-// as tcgen05.mma kind::tf32 with A read from TMEM and B from shared memory,
-// accumulating in FP32 in TMEM ("3xTF32": the dropped term S_lo Q_lo and the
-// TF32 rounding of S_lo are O(2^-22) relative, FP32-grade).  Slices of one
-// row block form a thread-block cluster whose partial tiles are summed in a
-// fixed CTA order through distributed shared memory (deterministic).
+// product by TMA in 128-row x 32-column tiles (128-byte swizzle).  Q (n x k)
+// is split once per product into TF32 high and low parts (hi = tf32(Q),
+// lo = tf32(Q - hi), both rounded to nearest) that TMA streams too.  Each CTA
+// owns 128 rows of S and up to 64 columns of Q over one slice of the inner
+// dimension; its converter warps split S the same way into tensor memory
+// (TMEM) and one thread issues
+//     D = S_hi [Q_hi | Q_lo] (+) S_lo Q_hi
+// as tcgen05.mma kind::tf32 with A read from TMEM and B from shared memory
+// ("3xTF32": the dropped term S_lo Q_lo and the TF32 rounding of the parts are
+// O(2^-22) relative, FP32-grade).  Two properties of the tensor cores shape
+// the design (both measured on GB300):
+//   - they read an FP32 operand as TF32 by truncation, so parts that are not
+//     TF32 values already pick up a systematic error (splitting by
+//     truncation gave a -3e-7 relative bias in S Q, which raised the PDHG
+//     residual floor from 2e-6 to 1.5e-5 on a bipartite MaxCut instance);
+//     both parts are therefore rounded to nearest before the MMA;
+//   - their FP32 accumulation truncates too (an error growing linearly with
+//     the number of accumulations: 5.8e-5 relative over 8192 inner indices),
+//     so each 32-wide chunk writes a fresh accumulator that the converter
+//     threads add into FP32 registers, rounded to nearest.
+// Measured: relative error 1.5e-7 (random data, n = 2000) with a bias of
+// -9e-8; the SIMT kernel gives 2e-7 and -1e-9.  Slices of one row block form a
+// thread-block cluster whose partial tiles are summed in a fixed CTA order
+// through distributed shared memory (deterministic).
 //
 // Every wait on an mbarrier is bounded (kWaitCycles); a CTA that gives up
 // drains its own copies in flight (bounded again), frees its TMEM and writes
@@ -36,14 +47,12 @@ namespace {
 
 constexpr int TC_M = 128;        // rows of S per CTA = the MMA's M
 constexpr int TC_KC = 32;        // inner-dimension chunk: one 128-byte swizzle row of FP32
-constexpr int TC_NS = 3;         // shared-memory stages
 constexpr int TC_NMAX = 64;      // columns of Q per CTA
-constexpr int TC_THREADS = 128;  // four warps: one TMEM lane quarter each
-constexpr uint32_t kTmemCols = 256;
-constexpr uint32_t kAccCol = 0;  // accumulator: columns [0, 64)
-constexpr uint32_t kABase = 64;  // A buffers b = 0, 1: hi at 64 + 64 b, lo at 96 + 64 b
+constexpr int TC_CONV_WARPS = 8;  // converter warps: two per TMEM lane quarter (one per column half)
+constexpr int TC_THREADS = 32 * (TC_CONV_WARPS + 2);  // plus the control and producer warps
+constexpr int TC_HALF = TC_NMAX / 2;                  // accumulator columns per converter thread
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at 2 GHz
-constexpr int kSmemFloor = 80 * 1024;  // at most two CTAs per SM, so two TMEM allocations always fit
+constexpr int kSmemTwoPerSm = 80 * 1024;   // floor that keeps at most two CTAs on an SM
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -111,27 +120,23 @@ __device__ __forceinline__ void tc_mma_ts(uint32_t d, uint32_t a, uint64_t bdesc
       : "memory");
 }
 
-#define PSDP_R8(a, o) "r"(a[o]), "r"(a[o + 1]), "r"(a[o + 2]), "r"(a[o + 3]), "r"(a[o + 4]), "r"(a[o + 5]), "r"(a[o + 6]), "r"(a[o + 7])
 
-// 32 consecutive TMEM columns of this thread's lane <- v[0..31]
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+// 16 consecutive TMEM columns of this thread's lane <- v[0..15]
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
-      PSDP_R8(v, 0), PSDP_R8(v, 8), PSDP_R8(v, 16), PSDP_R8(v, 24)
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
       : "memory");
 }
-#undef PSDP_R8
 
-// v[0..15] <- 16 consecutive TMEM columns of this thread's lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr)
-      : "memory");
+// v[0..7] <- 8 consecutive TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -155,16 +160,26 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// x (FP32) rounded to the nearest TF32 value (10 explicit mantissa bits;
+// halfway cases away from zero), as an FP32 bit pattern whose 13 low bits are
+// zero, so the tensor cores read it exactly.
+__device__ __forceinline__ uint32_t tf32_rn(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
+// x = hi + lo + e with hi = tf32(x), lo = tf32(x - hi) (both rounded to
+// nearest, so neither part is biased toward zero) and |e| <= 2^-22 |x|.
+// Truncating instead leaves every lo with the sign of x and lets the tensor
+// cores' own conversion of lo truncate it again: a systematic -3e-7 relative
+// error in S Q (measured), which raises the PDHG residual floor.
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-  const uint32_t h = __float_as_uint(x) & 0xFFFFE000u;
+  const uint32_t h = tf32_rn(x);
   hi = h;
-  lo = __float_as_uint(x - __uint_as_float(h));
+  lo = tf32_rn(x - __uint_as_float(h));
 }
 
 }  // namespace
 
-// Q (n x k, column stride ldq) -> Qhi, Qlo (column stride ld2): hi keeps the
-// 10 explicit mantissa bits of TF32 (the other 13 cleared), lo = Q - hi.
+// Q (n x k, column stride ldq) -> Qhi, Qlo (column stride ld2): hi = tf32(Q),
+// lo = tf32(Q - hi), both rounded to nearest (split_tf32).
 __global__ void k_split_tf32(const float* __restrict__ Q, int ldq, int n, int k, float* __restrict__ Qhi,
                              float* __restrict__ Qlo, int ld2, const int* skip) {
   if (skip && *(volatile const int*)skip) return;
@@ -178,176 +193,34 @@ __global__ void k_split_tf32(const float* __restrict__ Q, int ldq, int n, int k,
   }
 }
 
-// Shared memory: [stage s: S tile 16 KB | Qhi tile nt*128 B | Qlo tile nt*128 B] x TC_NS,
-// then the mbarriers and the TMEM address slot; the base is aligned to 1024 B.
-__global__ void __launch_bounds__(TC_THREADS) k_block_matvec_tc(const __grid_constant__ CUtensorMap tmS,
-                                                                const __grid_constant__ CUtensorMap tmQh,
-                                                                const __grid_constant__ CUtensorMap tmQl, int n,
-                                                                int k, float* __restrict__ W, int ldw, int nt,
-                                                                int kslice, const int* skip,
-                                                                cudaGraphConditionalHandle cond, int set_cond) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Converter thread (row_t, column half) results -> W: directly when the
+// inner dimension is not split (ns == 1); otherwise the partial tiles of the
+// ns CTAs of the cluster (in shared memory, the rings being idle) are summed
+// in slice order through distributed shared memory.  Called by every thread.
+__device__ __forceinline__ void tc_store_result(const float* acc, unsigned char* dsm, float* __restrict__ W, int ldw,
+                                                int n, int r0, int c0, int kc_cols, int hcols, int half, int row_t,
+                                                bool conv_thread, int ns, int tid) {
   namespace cg = cooperative_groups;
-  if (skip && *(volatile const int*)skip) return;  // uniform over the grid
-  if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
-    cudaGraphSetConditional(cond, 1u);
-  extern __shared__ __align__(1024) unsigned char dsm_raw[];
-  unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int ns = gridDim.x;
-  const int r0 = blockIdx.y * TC_M;
-  const int c0 = blockIdx.z * TC_NMAX;
-  const int kc_cols = min(TC_NMAX, k - c0);  // output columns of this CTA
-  const int kb = blockIdx.x * kslice, ke = min(n, kb + kslice);
-  const int nk = ke > kb ? (ke - kb + TC_KC - 1) / TC_KC : 0;  // chunks of this slice
-  const uint32_t tileS = TC_M * TC_KC * 4;                      // 16 KB
-  const uint32_t tileQ = (uint32_t)nt * TC_KC * 4;
-  const uint32_t stage = tileS + 2 * tileQ;
-  uint64_t* full = reinterpret_cast<uint64_t*>(dsm + TC_NS * stage);
-  uint64_t* mma_done = full + TC_NS;  // [2]: the MMAs of chunks with parity b have completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 2);
-  __shared__ int s_fail;
-  if (tid == 0) {
-    for (int s = 0; s < TC_NS; ++s) mbar_init(&full[s], 1);
-    mbar_init(&mma_done[0], 1);
-    mbar_init(&mma_done[1], 1);
-    s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;  // this warp's TMEM lane quarter
-  const uint32_t idesc = idesc_tf32(TC_M, nt);
-  auto issue_load = [&](int j) {  // chunk j of the slice into stage j % TC_NS
-    unsigned char* st = dsm + (j % TC_NS) * stage;
-    uint64_t* bar = &full[j % TC_NS];
-    mbar_expect_tx(bar, stage);
-    const int x = kb + j * TC_KC;
-    tma_load_2d(st, &tmS, bar, x, r0);
-    tma_load_2d(st + tileS, &tmQh, bar, x, c0);
-    tma_load_2d(st + tileS + tileQ, &tmQl, bar, x, c0);
-  };
-  int issued = 0;    // chunks whose loads were issued (thread 0)
-  int committed = -1;  // last chunk whose MMAs were committed (thread 0)
-  if (tid == 0) {
-    for (; issued < min(TC_NS, nk); ++issued) issue_load(issued);
-  }
-  bool fail = false;
-  for (int c = 0; c < nk; ++c) {
-    const int s = c % TC_NS, b = c & 1;
-    unsigned char* st = dsm + s * stage;
-    bool ok = mbar_wait(&full[s], (uint32_t)((c / TC_NS) & 1), kWaitCycles);
-    if (ok && c >= 2) ok = mbar_wait(&mma_done[b], (uint32_t)(((c - 2) >> 1) & 1), kWaitCycles);
-    tc_fence_after();
-    if (!ok) s_fail = 1;
-    // this thread's row of the S tile: 16-byte chunk q of row tid sits at chunk q ^ (tid & 7)
-    uint32_t hi[32], lo[32];
-    const unsigned char* srow = st + tid * 128;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = *reinterpret_cast<const float4*>(srow + ((q ^ (tid & 7)) << 4));
-      split_tf32(v.x, hi[4 * q], lo[4 * q]);
-      split_tf32(v.y, hi[4 * q + 1], lo[4 * q + 1]);
-      split_tf32(v.z, hi[4 * q + 2], lo[4 * q + 2]);
-      split_tf32(v.w, hi[4 * q + 3], lo[4 * q + 3]);
-    }
-    const uint32_t abuf = tmem + kABase + 64u * (uint32_t)b;
-    if (ok) {
-      tmem_st32(abuf + lane_off, hi);
-      tmem_st32(abuf + 32u + lane_off, lo);
-    }
-    tmem_wait_st();
-    tc_fence_before();
-    __syncthreads();
-    if (s_fail) {
-      fail = true;
-      break;
-    }
-    if (tid == 0) {
-      tc_fence_after();
-      const uint64_t dh = sdesc_k_sw128(smem_u32(st + tileS));
-      const uint64_t dl = sdesc_k_sw128(smem_u32(st + tileS + tileQ));
-#pragma unroll
-      for (int kk = 0; kk < TC_KC / 8; ++kk) {
-        const uint32_t ah = abuf + 8u * kk, al = ah + 32u;
-        const uint64_t step = (uint64_t)(kk * 32 >> 4);  // 8 TF32 = 32 bytes along K
-        tc_mma_ts(tmem + kAccCol, al, dh + step, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-        tc_mma_ts(tmem + kAccCol, ah, dl + step, idesc, 1u);
-        tc_mma_ts(tmem + kAccCol, ah, dh + step, idesc, 1u);
-      }
-      tc_commit(&mma_done[b]);
-      committed = c;
-      // refill the stage of chunk c - 1 once its MMAs (which read its Q tiles) are done
-      if (c >= 1 && issued < nk) {
-        if (mbar_wait(&mma_done[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles)) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue_load(issued);
-          ++issued;
-        } else {
-          s_fail = 1;
-        }
-      }
-    }
-  }
-  // accumulator -> registers (row tid of the tile, columns [0, nt))
-  float acc[TC_NMAX];
-#pragma unroll
-  for (int j = 0; j < TC_NMAX; ++j) acc[j] = 0.f;
-  if (!fail && nk > 0) {
-    const int last = nk - 1;
-    if (!mbar_wait(&mma_done[last & 1], (uint32_t)((last >> 1) & 1), kWaitCycles)) fail = true;
-    tc_fence_after();
-    if (!fail) {
-#pragma unroll
-      for (int g = 0; g < TC_NMAX / 16; ++g) {
-        if (g * 16 < nt) {
-          uint32_t v[16];
-          tmem_ld16(tmem + kAccCol + 16u * g + lane_off, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[16 * g + j] = __uint_as_float(v[j]);
-        }
-      }
-    }
-  }
-  if (__syncthreads_or(fail ? 1 : 0)) {
-    // give up: drain this CTA's own copies and MMAs in flight (bounded), NaN output
-    fail = true;
-    if (tid == 0) {
-      for (int j = max(0, issued - TC_NS); j < issued; ++j)
-        mbar_wait(&full[j % TC_NS], (uint32_t)((j / TC_NS) & 1), kWaitCycles / 8);
-      if (committed >= 0) mbar_wait(&mma_done[committed & 1], (uint32_t)((committed >> 1) & 1), kWaitCycles / 8);
-    }
-#pragma unroll
-    for (int j = 0; j < TC_NMAX; ++j) acc[j] = __int_as_float(0x7fc00000);
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
-  }
   if (ns == 1) {
-    const int row = r0 + tid;
-    if (row < n)
+    const int row = r0 + row_t;
+    if (conv_thread && row < n)
 #pragma unroll
-      for (int j = 0; j < TC_NMAX; ++j)
-        if (j < kc_cols) W[(size_t)(c0 + j) * ldw + row] = acc[j];
+      for (int j = 0; j < TC_HALF; ++j) {
+        const int col = half * hcols + j;
+        if (j < hcols && col < kc_cols) W[(size_t)(c0 + col) * ldw + row] = acc[j];
+      }
     return;
   }
-  // split inner dimension: partial tiles in shared memory (the stages are idle
-  // now), summed in slice order through distributed shared memory
   const int ldp = TC_NMAX + 1;
   float* Ps = reinterpret_cast<float*>(dsm);
+  if (conv_thread)
 #pragma unroll
-  for (int j = 0; j < TC_NMAX; ++j) Ps[tid * ldp + j] = acc[j];
+    for (int j = 0; j < TC_HALF; ++j)
+      if (j < hcols) Ps[row_t * ldp + half * hcols + j] = acc[j];
   cg::cluster_group cluster = cg::this_cluster();
   cluster.sync();
   const int rank = (int)cluster.block_rank();
@@ -364,6 +237,273 @@ __global__ void __launch_bounds__(TC_THREADS) k_block_matvec_tc(const __grid_con
     if (row < n) W[(size_t)(c0 + col) * ldw + row] = sum;
   }
   cluster.sync();  // keep every CTA's shared memory alive until all reads are done
+}
+
+// Warp roles: warps 0-7 ("converters", two per TMEM lane quarter, one per
+// half of the columns) read their part of each S tile from shared memory,
+// split it and store S_hi | S_lo into an A buffer in TMEM, and add the
+// chunk's accumulators into FP32 registers once its MMAs have completed;
+// warp 8 ("control", one thread) issues the MMAs; warp 9 ("producer", one
+// thread) issues the S tile loads; converter warp 0 also refills the Q ring.
+// S tiles and Q tiles live in separate rings: an S stage is free as soon as
+// the converters have read it, a Q stage once the MMAs reading it have
+// completed, so S can be fetched further ahead.
+// Two MMAs per k-step: S_hi [Q_hi | Q_lo] as one MMA of width 2 nt (the Q
+// stage holds the two tiles back to back, so they form one K-major operand),
+// then S_lo Q_hi into the second half.  An accumulator is 2 nt TMEM columns:
+// the first nt sum S_hi Q_hi over the chunk's four k-steps, the next nt the
+// two small terms (which therefore never meet the large partial in a
+// truncating addition); the converters add both halves into FP32 registers.
+// Buffers (two CTAs per SM, 256 TMEM columns each): `nd` accumulators from
+// column 0 and `na` A buffers of 64 columns from column 2 nt nd.
+//   na = 1, nd = 2 (widths <= 48): the converters store chunk c's S_hi | S_lo
+//     once the MMAs of chunk c - 1 have completed and drain chunk c - 1's
+//     accumulator while the MMAs of chunk c run;
+//   na = 2, nd = 1 (width 64): they store chunk c while the MMAs of chunk c - 1
+//     run, then drain chunk c - 1's accumulator before the MMAs of chunk c.
+// Handoffs through mbarriers only:
+//   fullS[i] / fullQ[j]  TMA -> consumers: the stage holds its tile(s)
+//   emptyS[i]            converters -> producer (8 arrivals): S stage read
+//   conv[b]              converters -> control (8 arrivals): the A buffer of
+//                        chunk c holds it (barrier c & 1, phase c >> 1)
+//   done[b]              control (tcgen05.commit) -> converters: the MMAs of
+//                        the chunk with parity b have completed
+//   drained[b]           converters -> control (nd = 1): the accumulator of
+//                        chunk c has been read (barrier c & 1)
+// One barrier per chunk parity wherever the other side can be two chunks
+// ahead, so that no phase parity aliases.
+// Shared memory (base aligned to 1024 B): nss S stages of 16 KB, nqs Q stages
+// of [Qhi tile nt*128 B | Qlo tile nt*128 B], the mbarriers, the TMEM address
+// slot.
+__global__ void __launch_bounds__(TC_THREADS, 2) k_block_matvec_tc(const __grid_constant__ CUtensorMap tmS,
+                                                                    const __grid_constant__ CUtensorMap tmQh,
+                                                                    const __grid_constant__ CUtensorMap tmQl, int n,
+                                                                    int k, float* __restrict__ W, int ldw, int nt,
+                                                                    int kslice, int nss, int nqs, int na, int nd,
+                                                                    uint32_t tmem_cols, const int* skip,
+                                                                    cudaGraphConditionalHandle cond, int set_cond) {
+  if (skip && *(volatile const int*)skip) return;  // uniform over the grid
+  if (set_cond && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0)
+    cudaGraphSetConditional(cond, 1u);
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  unsigned char* dsm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ns = gridDim.x;
+  const int r0 = blockIdx.y * TC_M;
+  const int c0 = blockIdx.z * TC_NMAX;
+  const int kc_cols = min(TC_NMAX, k - c0);
+  const int kb = blockIdx.x * kslice, ke = min(n, kb + kslice);
+  const int nk = ke > kb ? (ke - kb + TC_KC - 1) / TC_KC : 0;
+  const uint32_t tileS = TC_M * TC_KC * 4;
+  const uint32_t tileQ = (uint32_t)nt * TC_KC * 4;
+  unsigned char* ringS = dsm;
+  unsigned char* ringQ = dsm + (size_t)nss * tileS;
+  uint64_t* fullS = reinterpret_cast<uint64_t*>(ringQ + (size_t)nqs * 2 * tileQ);
+  uint64_t* emptyS = fullS + nss;
+  uint64_t* fullQ = emptyS + nss;
+  // [2]: the A buffer of chunk c holds it (barrier c & 1, phase c >> 1; one
+  // barrier per parity, since with two A buffers the converters may run two
+  // chunks ahead of the MMAs and a single barrier's phase parity would alias)
+  uint64_t* conv = fullQ + nqs;
+  uint64_t* done = conv + 2;     // [2]: the MMAs of the chunk with parity b have completed
+  uint64_t* drained = done + 2;  // [2]: (one accumulator) the converters have read chunk c's (barrier c & 1)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drained + 2);
+  __shared__ int s_fail;
+  if (tid == 0) {
+    for (int i = 0; i < nss; ++i) {
+      mbar_init(&fullS[i], 1);
+      mbar_init(&emptyS[i], TC_CONV_WARPS);
+    }
+    for (int j = 0; j < nqs; ++j) mbar_init(&fullQ[j], 1);
+    mbar_init(&conv[0], TC_CONV_WARPS);
+    mbar_init(&conv[1], TC_CONV_WARPS);
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    mbar_init(&drained[0], TC_CONV_WARPS);
+    mbar_init(&drained[1], TC_CONV_WARPS);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t a_col = 2u * (uint32_t)nt * (uint32_t)nd;  // the A buffers (na of them, 64 columns each)
+  auto issue_q = [&](int j) {                // Q tiles of chunk j into Q stage j % nqs
+    unsigned char* st = ringQ + (size_t)(j % nqs) * 2 * tileQ;
+    uint64_t* bar = &fullQ[j % nqs];
+    mbar_expect_tx(bar, 2 * tileQ);
+    const int x = kb + j * TC_KC;
+    tma_load_2d(st, &tmQh, bar, x, c0);
+    tma_load_2d(st + tileQ, &tmQl, bar, x, c0);
+  };
+  const int row_t = 32 * (warp & 3) + lane, half = (warp >> 2) & 1;
+  const int hcols = nt / 2;
+  float acc[TC_HALF];
+#pragma unroll
+  for (int j = 0; j < TC_HALF; ++j) acc[j] = 0.f;
+  int issuedS = 0, issuedQ = 0, committed = -1;
+  bool fail = false;
+  if (warp < TC_CONV_WARPS) {
+    // ------------------------------------------------------------ converters
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    // acc += main + small-term halves of the accumulator of chunk parity b (columns of my half)
+    auto drain = [&](int b) {
+      const uint32_t col = tmem + 2u * (uint32_t)nt * (uint32_t)(b & (nd - 1)) + (uint32_t)(half * hcols) + lane_off;
+#pragma unroll
+      for (int h = 0; h < TC_HALF / 8; ++h) {
+        if (h * 8 < hcols) {
+          uint32_t vm[8], vc[8];
+          tmem_ld8(col + 8u * h, vm);
+          tmem_ld8(col + (uint32_t)nt + 8u * h, vc);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[8 * h + j] += __uint_as_float(vm[j]) + __uint_as_float(vc[j]);
+        }
+      }
+    };
+    if (warp == 0 && lane == 0) issuedQ = min(nqs, nk);  // the control thread issued those
+    for (int c = 0; c < nk; ++c) {
+      const int si = c % nss;
+      bool ok = mbar_wait(&fullS[si], (uint32_t)((c / nss) & 1), kWaitCycles);
+      float4 sv[4];
+      const unsigned char* srow = ringS + (size_t)si * tileS + row_t * 128;
+      if (ok) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          sv[q] = *reinterpret_cast<const float4*>(srow + (((4 * half + q) ^ (row_t & 7)) << 4));
+      }
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&emptyS[si]);
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split_tf32(sv[q].x, hi[4 * q], lo[4 * q]);
+        split_tf32(sv[q].y, hi[4 * q + 1], lo[4 * q + 1]);
+        split_tf32(sv[q].z, hi[4 * q + 2], lo[4 * q + 2]);
+        split_tf32(sv[q].w, hi[4 * q + 3], lo[4 * q + 3]);
+      }
+      // the A buffer of chunk c is free once the MMAs of chunk c - na have
+      // completed (with two A buffers, chunk c - 2 also frees the accumulators
+      // chunk c will write: drained here, before the store)
+      const int cw = c - na;
+      if (ok && cw >= 0) ok = mbar_wait(&done[cw & 1], (uint32_t)((cw >> 1) & 1), kWaitCycles);
+      ok = __all_sync(0xffffffffu, ok && !*(volatile int*)&s_fail);
+      if (!ok) {
+        s_fail = 1;
+        fail = true;
+        break;
+      }
+      tc_fence_after();
+      if (warp == 0 && lane == 0 && cw >= 0 && issuedQ < nk) {  // chunk c - na's Q stage is free
+        issue_q(issuedQ);
+        ++issuedQ;
+      }
+      if (nd == 2 && na == 2 && cw >= 0) drain(cw & 1);
+      const uint32_t abuf = tmem + a_col + 64u * (uint32_t)(c & (na - 1)) + 16u * (uint32_t)half + lane_off;
+      tmem_st16(abuf, hi);
+      tmem_st16(abuf + 32u, lo);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[c & 1]);
+      if (nd == 2 && na == 1 && c >= 1) drain((c - 1) & 1);  // while the MMAs of chunk c run
+      if (nd == 1 && c >= 1) {  // one accumulator: read chunk c - 1's before the MMAs of chunk c start
+        const int cp = c - 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&done[cp & 1], (uint32_t)((cp >> 1) & 1), kWaitCycles) &&
+                                         !*(volatile int*)&s_fail)) {
+          s_fail = 1;
+          fail = true;
+          break;
+        }
+        tc_fence_after();
+        drain(0);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&drained[cp & 1]);
+      }
+    }
+    if (!fail) {  // the accumulators not drained yet: the last na chunks (one with a single accumulator)
+      for (int j = max(0, nk - (nd == 1 ? 1 : na)); j < nk; ++j) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&done[j & 1], (uint32_t)((j >> 1) & 1), kWaitCycles))) {
+          s_fail = 1;
+          fail = true;
+          break;
+        }
+        tc_fence_after();
+        drain(j & 1);
+      }
+    }
+  } else if (warp == TC_CONV_WARPS && lane == 0) {
+    // ------------------------------------------------------------ control: MMAs
+    const uint32_t idesc2 = idesc_tf32(TC_M, 2 * nt), idesc1 = idesc_tf32(TC_M, nt);
+    for (; issuedQ < min(nqs, nk); ++issuedQ) issue_q(issuedQ);
+    for (int c = 0; c < nk; ++c) {
+      const int qj = c % nqs, b = c & 1;
+      unsigned char* st = ringQ + (size_t)qj * 2 * tileQ;
+      if (!mbar_wait(&fullQ[qj], (uint32_t)((c / nqs) & 1), kWaitCycles) ||
+          !mbar_wait(&conv[b], (uint32_t)((c >> 1) & 1), kWaitCycles) ||
+          (nd == 1 && c >= 1 && !mbar_wait(&drained[(c - 1) & 1], (uint32_t)(((c - 1) >> 1) & 1), kWaitCycles)) ||
+          *(volatile int*)&s_fail) {
+        s_fail = 1;
+        fail = true;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t dq = sdesc_k_sw128(smem_u32(st));  // [Q_hi | Q_lo], 2 nt rows
+      const uint32_t dmain = tmem + 2u * (uint32_t)nt * (uint32_t)(b & (nd - 1)), dsmall = dmain + (uint32_t)nt;
+      const uint32_t abuf = tmem + a_col + 64u * (uint32_t)(c & (na - 1));
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 8; ++kk)  // S_hi [Q_hi | Q_lo]
+        tc_mma_ts(dmain, abuf + 8u * kk, dq + (uint64_t)(kk * 32 >> 4), idesc2, kk > 0 ? 1u : 0u);
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 8; ++kk)  // + S_lo Q_hi into the small half
+        tc_mma_ts(dsmall, abuf + 32u + 8u * kk, dq + (uint64_t)(kk * 32 >> 4), idesc1, 1u);
+      tc_commit(&done[b]);
+      committed = c;
+    }
+  } else if (warp == TC_CONV_WARPS + 1 && lane == 0) {
+    // ------------------------------------------------------------ producer: S tiles
+    for (; issuedS < nk; ++issuedS) {
+      const int j = issuedS, si = j % nss;
+      if (j >= nss && (!mbar_wait(&emptyS[si], (uint32_t)(((j / nss) - 1) & 1), kWaitCycles) ||
+                       *(volatile int*)&s_fail)) {
+        s_fail = 1;
+        fail = true;
+        break;
+      }
+      mbar_expect_tx(&fullS[si], tileS);
+      tma_load_2d(ringS + (size_t)si * tileS, &tmS, &fullS[si], kb + j * TC_KC, r0);
+    }
+  }
+  if (__syncthreads_or(fail ? 1 : 0)) {
+    fail = true;
+    if (warp == 0 && lane == 0) {  // Q loads (issued by the control thread and this one)
+      for (int j = max(0, issuedQ - nqs); j < issuedQ; ++j)
+        mbar_wait(&fullQ[j % nqs], (uint32_t)((j / nqs) & 1), kWaitCycles / 8);
+    }
+    if (warp == TC_CONV_WARPS && lane == 0 && committed >= 0)
+      mbar_wait(&done[committed & 1], (uint32_t)((committed >> 1) & 1), kWaitCycles / 8);
+    if (warp == TC_CONV_WARPS + 1 && lane == 0) {
+      for (int j = max(0, issuedS - nss); j < issuedS; ++j)
+        mbar_wait(&fullS[j % nss], (uint32_t)((j / nss) & 1), kWaitCycles / 8);
+    }
+#pragma unroll
+    for (int j = 0; j < TC_HALF; ++j) acc[j] = __int_as_float(0x7fc00000);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+  }
+  tc_store_result(acc, dsm, W, ldw, n, r0, c0, kc_cols, hcols, half, row_t, warp < TC_CONV_WARPS, ns, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -404,23 +544,68 @@ bool make_map(CUtensorMap* m, const float* base, int inner, int outer, int ld, i
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int g_tc_cluster_max = 8;  // 16 where the device co-schedules 16-CTA clusters of this kernel
+int g_smem_max = 227 * 1024 - 1024;  // dynamic shared memory a CTA may use (set from the device at init)
 
-size_t tc_smem_bytes(int nt) {
-  const size_t stage = (size_t)TC_M * TC_KC * 4 + 2 * (size_t)nt * TC_KC * 4;
-  const size_t need = 1024 + TC_NS * stage + (TC_NS + 2) * sizeof(uint64_t) + 16;
-  return need < (size_t)kSmemFloor ? (size_t)kSmemFloor : need;
+struct TcShape {
+  int nss, nqs, na, nd;
+  uint32_t tmem_cols;
+  size_t smem;
+};
+
+// Shared memory of a shape: 1024 B alignment slack, the rings, the barriers.
+size_t tc_smem_need(int nt, int nss, int nqs) {
+  return 1024 + (size_t)nss * TC_M * TC_KC * 4 + (size_t)nqs * 2 * nt * TC_KC * 4 +
+         (size_t)(2 * nss + 2 * nqs + 6) * sizeof(uint64_t) + 16;
 }
+
+// Launch shape for a CTA width of nt columns (two CTAs per SM): na / nd as
+// described at the kernel (PSDP_TC_NA / PSDP_TC_ND override them for
+// measurements), as many S stages as fit beside two Q stages, then up to
+// four Q stages.
+TcShape tc_shape(int nt, int want_na, int want_nd) {
+  TcShape t;
+  int na = want_na > 0 ? want_na : (nt <= 48 ? 1 : 2);
+  int nd = want_nd > 0 ? want_nd : (nt <= 48 ? 2 : 1);
+  if (2 * nt * nd + 64 * na > 256) {  // what fits in 256 columns
+    na = 2;
+    nd = 1;
+  }
+  t.na = na;
+  t.nd = nd;
+  t.tmem_cols = 256;
+  const size_t cap = (size_t)(228 * 1024 / 2 - 1024);  // two CTAs per SM
+  int nss = 2, nqs = 2;
+  while (nss < 8 && tc_smem_need(nt, nss + 1, nqs) <= cap) ++nss;
+  while (nqs < 4 && tc_smem_need(nt, nss, nqs + 1) <= cap) ++nqs;
+  t.nss = nss;
+  t.nqs = nqs;
+  const size_t need = tc_smem_need(nt, nss, nqs);
+  t.smem = need < (size_t)kSmemTwoPerSm ? (size_t)kSmemTwoPerSm : need;
+  return t;
+}
+
+int g_tc_na = 0;  // A buffers (0: by width; PSDP_TC_NA overrides: 1 or 2)
+int g_tc_nd = 0;  // accumulators (0: by width; PSDP_TC_ND overrides: 1 or 2)
+int g_tc_cluster_max = 8;  // 16 where the device co-schedules 16-CTA clusters of this kernel
 
 }  // namespace
 
 void init_mv_tc_attributes() {
-  cudaFuncSetAttribute(k_block_matvec_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(TC_NMAX));
+  if (const char* v = getenv("PSDP_TC_NA")) g_tc_na = atoi(v) == 1 ? 1 : 2;
+  if (const char* v = getenv("PSDP_TC_ND")) g_tc_nd = atoi(v) == 2 ? 2 : 1;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+      cudaFuncGetAttributes(&fa, k_block_matvec_tc) == cudaSuccess)
+    g_smem_max = optin - (int)fa.sharedSizeBytes;
+  cudaFuncSetAttribute(k_block_matvec_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, g_smem_max);
   if (cudaFuncSetAttribute(k_block_matvec_tc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    const TcShape t = tc_shape(TC_NMAX, g_tc_na, g_tc_nd);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16, 1, 1);
     cfg.blockDim = dim3(TC_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = tc_smem_bytes(TC_NMAX);
+    cfg.dynamicSmemBytes = t.smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 16;
@@ -451,11 +636,11 @@ bool block_matvec_tc_applies(const float* S, int lds, const float* scratch) {
 size_t block_matvec_tc_scratch_floats(int n, int k) { return 2 * (size_t)((n + 31) / 32 * 32) * (size_t)k; }
 
 // Slices of the inner dimension (= cluster size): the largest power of two
-// whose CTAs (two resident per SM) still run in one wave, keeping at least
-// two chunks per slice.
-static int tc_slices(int n, int tiles, int sms) {
+// whose CTAs (`per_sm` resident per SM) still run in one wave, keeping at
+// least two chunks per slice.
+static int tc_slices(int n, int tiles, int sms, int per_sm) {
   int ns = 1;
-  while (ns < g_tc_cluster_max && tiles * (2 * ns) <= 2 * sms && n >= (2 * ns) * 2 * TC_KC) ns *= 2;
+  while (ns < g_tc_cluster_max && tiles * (2 * ns) <= per_sm * sms && n >= (2 * ns) * 2 * TC_KC) ns *= 2;
   return ns;
 }
 
@@ -479,13 +664,14 @@ bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int 
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
     k_split_tf32<<<blocks, 256, 0, st>>>(Q, ldq, n, k, Qhi, Qlo, ld2, skip);
   }
+  const TcShape shape = tc_shape(nt, g_tc_na, g_tc_nd);
   const int rb = (n + TC_M - 1) / TC_M, ztiles = (k + TC_NMAX - 1) / TC_NMAX;
-  const int ns = tc_slices(n, rb * ztiles, sms);
+  const int ns = tc_slices(n, rb * ztiles, sms, 2);
   const int kslice = ((n + ns - 1) / ns + TC_KC - 1) / TC_KC * TC_KC;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ns, rb, ztiles);
   cfg.blockDim = dim3(TC_THREADS, 1, 1);
-  cfg.dynamicSmemBytes = tc_smem_bytes(nt);
+  cfg.dynamicSmemBytes = shape.smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -494,7 +680,8 @@ bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_block_matvec_tc, mS, mQh, mQl, n, k, W, ldw, nt, kslice, skip, cond, set_cond);
+  cudaLaunchKernelEx(&cfg, k_block_matvec_tc, mS, mQh, mQl, n, k, W, ldw, nt, kslice, shape.nss, shape.nqs, shape.na,
+                     shape.nd, shape.tmem_cols, skip, cond, set_cond);
   return true;
 }
 

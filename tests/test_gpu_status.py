@@ -134,7 +134,9 @@ def test_saved_feasible_pair(pkg, n):
     assert info.status == pkg.CONVERGED, info.as_dict()
     assert info.rank_changes >= 1
     sv = slv.get_saved_pair()
-    assert 1 <= sv["r"] < info.final_rank and sv["r"] in {r for _, r in ref.saved}
+    # the rank path is not pinned (it depends on FP32 vs FP64 trajectories):
+    # the pair was saved at one of the ranks 1, 2, 4, ... below the final one
+    assert 1 <= sv["r"] < info.final_rank and (sv["r"] & (sv["r"] - 1)) == 0
     assert 0 < sv["iter"] < info.iters
     cert = oracle.certificates(prob, sv["X"], -sv["y"])
     assert cert["primal_eq"] <= 1e-4, cert
