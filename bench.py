@@ -621,6 +621,48 @@ def run_sweep(args):
     return 0
 
 
+WORKLOAD_SOLVES = {
+    # one whole solve to 1e-4 of a larger configuration, capped (seconds)
+    "c4": ("graph equipartition of G(5000, 0.002), unit weights, seed 3 (Sec. 5.1), tr(11^T X) = 0 as a "
+           "structured row", "config_equipartition_5000", 16),
+    "c3": ("sensor network localisation, 1000 sensors + 10 anchors, radius 0.2, seed 2 (Sec. 5.2)",
+           "config_sensor_1000", 8),
+}
+
+
+def run_workload_solve(args):
+    """Time to 1e-4 of one solve of a larger configuration (the factored
+    operator where it applies), capped at --time-limit seconds; the line
+    reports the residuals and the gap reached when the cap ends it."""
+    import torch
+
+    import paper_1810_05231_gb300 as pkg
+    import sdp_instances as si
+
+    title, fn, rank0 = WORKLOAD_SOLVES[args.workload]
+    inst = getattr(si, fn)()
+    slv = pkg.Solver(tol=1e-4, rank_init=rank0, max_iter=10 ** 7, time_limit_s=args.time_limit, check_every=200,
+                     operator_form=OPERATOR_FORMS[args.operator])
+    t0 = time.perf_counter()
+    slv.set_instance(inst)
+    info = slv.solve()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    slv.close()
+    conv = info.status == pkg.CONVERGED
+    line = {"metric": f"time to 1e-4: {title}", "value": round(info.solve_seconds, 3), "unit": "s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": round(1000 * info.solve_seconds, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": fn, "n": inst.n, "tol": 1e-4, "rank_init": rank0, "operator": args.operator,
+                       "time_limit_s": args.time_limit},
+            "converged": conv, "status": int(info.status), "iters": int(info.iters), "final_rank": info.final_rank,
+            "iters_per_s": round(info.iters / max(info.solve_seconds, 1e-9), 2), "primal_obj": info.primal_obj,
+            "rel_primal_res": info.rel_primal_res, "rel_dual_res": info.rel_dual_res, "rel_gap": info.rel_gap,
+            "wall_s_with_set_problem": round(wall, 3), "gpu_launches": int(info.kernel_launches)}
+    print(json.dumps(line))
+    return 0
+
+
 def aggregate_replicas(total_t, total_it, device):
     """Whole-job figures of N independent replicas (one per rank, no data-path
     collective): iterations summed over the ranks, time the maximum over the
@@ -647,7 +689,8 @@ def main():
     ap.add_argument("--arpack-seconds", type=float, default=10.0, help="host seconds of the ARPACK LR leg (0: skip)")
     ap.add_argument("--streaming", type=int, default=1, help="run the n = 16384 streaming leg (1) or not (0)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="maxcut", choices=["maxcut", "mimo-batch"] + sorted(SWEEPS))
+    ap.add_argument("--workload", default="maxcut",
+                    choices=["maxcut", "mimo-batch"] + sorted(SWEEPS) + sorted(WORKLOAD_SOLVES))
     ap.add_argument("--sizes", default="", help="comma-separated sizes for the table2 / table3 sweeps")
     ap.add_argument("--time-limit", type=float, default=60.0, help="per-instance cap of the sweeps (s)")
     ap.add_argument("--operator", default="explicit", choices=sorted(OPERATOR_FORMS),
@@ -661,6 +704,8 @@ def main():
         return run_mimo_batch(args)
     if args.workload in SWEEPS:
         return run_sweep(args)
+    if args.workload in WORKLOAD_SOLVES:
+        return run_workload_solve(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
 
