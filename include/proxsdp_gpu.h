@@ -100,7 +100,8 @@ typedef struct {
   int precision;          /* PROXSDP_PREC_FP32                                           [0]   */
   int normalize_rows;     /* scale each (A_i, rhs_i) to ||A_i||_F = 1                    [1]   */
   uint64_t seed;          /* Lanczos start block                                         [1]   */
-  int max_rank;           /* cap on the target rank (Lanczos path: <= 60)                [60]  */
+  int max_rank;           /* cap on the target rank; the Lanczos path (n > 128) holds
+                             at most 64, or 60 with the factored operator                [64]  */
   int lanczos_steps;      /* block Krylov steps per restart cycle (0: automatic)         [0]   */
   int lanczos_max_cycles; /* restart cycles per projection                               [8]   */
   double lanczos_tol;     /* Ritz residual tolerance relative to |theta_1| (0: adaptive) [0]   */
@@ -213,8 +214,10 @@ int proxsdp_gpu_get_saved_pair(proxsdp_gpu_t h, double* X, double* y, double* V,
 
 /* Set the iterate (X = V diag(max(lambda,0)) V^T with V n*r column-major,
  * orthonormal columns, and y in the paper's dual sign / original scaling) and
- * the target rank, so that proxsdp_gpu_iterate continues from it.  Used for
- * one-step parity against Alg. 1 / Alg. 2. */
+ * the target rank, so that proxsdp_gpu_iterate continues from it (one-step
+ * parity against Alg. 1 / Alg. 2, or resuming from a saved pair).  On the
+ * block Lanczos path (n > 128) r <= 64, or r <= 60 with the factored
+ * operator; larger r returns PROXSDP_ERR_UNSUPPORTED. */
 int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const double* lambda,
                             const double* y);
 

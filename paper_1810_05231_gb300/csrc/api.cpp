@@ -456,7 +456,7 @@ int proxsdp_gpu_settings_default(proxsdp_gpu_settings* s) {
   s->precision = PROXSDP_PREC_FP32;
   s->normalize_rows = 1;
   s->seed = 1;
-  s->max_rank = 60;
+  s->max_rank = 64;
   s->lanczos_steps = 0;
   s->lanczos_max_cycles = 8;
   s->lanczos_tol = 0.0;
@@ -581,6 +581,10 @@ int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const doubl
   if (!S.has_problem) return S.fail(PROXSDP_ERR_BAD_STATE, "set_iterate before set_problem");
   if (r < 1 || r > std::min(S.hp.n, psdp::kMaxR) || (!V && r > 0) || !lambda)
     return S.fail(PROXSDP_ERR_INVALID_ARG, "bad rank or NULL factors");
+  if (S.hp.n > psdp::kFullEigMax && !S.set.full_eig &&
+      r > (S.factored ? psdp::kMaxRankFactored : psdp::kMaxRankLanczos))
+    return S.fail(PROXSDP_ERR_UNSUPPORTED, S.factored ? "rank above 60 with the factored operator"
+                                                      : "rank above 64 on the block Lanczos path");
   cudaSetDevice(S.device);
   return S.set_iterate(r, V, lambda, y);
 }

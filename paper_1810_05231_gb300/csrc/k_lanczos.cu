@@ -300,6 +300,35 @@ void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned lon
 }
 
 // ---------------------------------------------------------------------------
+// expansion block of a wide kept block
+// ---------------------------------------------------------------------------
+// When the kept Ritz block is wider than the Krylov block (w > kMaxW), one
+// restart cycle expands the basis by b < w directions: the columns
+// (off + j) mod w, j < b, of W = S Q_kept, with the offset advancing by b
+// with every restart cycle (the cycle count comes from the control block).
+// Orthogonalised against Q_kept they are the residual directions of those b
+// Ritz pairs, i.e. one block Lanczos step for them, and over w / b
+// successive cycles every kept pair gets one.
+__global__ void __launch_bounds__(256) k_compress_block(const float* __restrict__ W, int ldw, int w,
+                                                        float* __restrict__ Z, int ldz, int b, int n,
+                                                        const Ctl* ctl, const int* skip) {
+  if (skip && *(volatile const int*)skip) return;
+  const int off = (int)(((long long)ctl->lz_cycles_total * b) % w);
+  const size_t total = (size_t)n * b;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / n), i = (int)(idx % n);
+    Z[(size_t)j * ldz + i] = W[(size_t)((off + j) % w) * ldw + i];
+  }
+}
+
+void launch_compress_block(const float* W, int ldw, int w, float* Z, int ldz, int b, int n, const Ctl* ctl,
+                           const int* skip, cudaStream_t st) {
+  const size_t total = (size_t)n * b;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  k_compress_block<<<blocks, 256, 0, st>>>(W, ldw, w, Z, ldz, b, n, ctl, skip);
+}
+
+// ---------------------------------------------------------------------------
 // Gram H = A^T B with exact-product accumulation
 // ---------------------------------------------------------------------------
 // Grid (output tiles, row splits); the row splits of one 16 x 16 output tile

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   float* Ys = Ws + RZ_RB * ldk;        // K x w
   float* Vs = Ys + K * w;              // RB x (w+1)
   float* WVs = Vs + RZ_RB * (w + 1);   // RB x (w+1)
-  __shared__ double th[kMaxW];
+  __shared__ double th[kMaxP];
   const int tid = threadIdx.x;
   const int r0 = blockIdx.x * RZ_RB;
   const int rows = min(RZ_RB, n - r0);
@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   __syncthreads();
   {  // V = Q Y and W Y on this CTA's rows: 2 rows x (w/16) columns per thread
     const int ti = tid >> 4, tt = tid & 15;  // rows ti, ti + 16; columns tt + 16 j
-    const int wg = (w + 15) / 16;
-    float v[2][4] = {}, u[2][4] = {};
+    const int wg = (w + 15) / 16;            // <= kMaxP / 16 = 7
+    float v[2][kMaxP / 16] = {}, u[2][kMaxP / 16] = {};
     const float* q0 = Qs + ti * ldk;
     const float* q1 = Qs + (ti + 16) * ldk;
     const float* w0 = Ws + ti * ldk;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
     for (int k = 0; k < K; ++k) {
       const float a0 = q0[k], a1 = q1[k], b0 = w0[k], b1 = w1[k];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < kMaxP / 16; ++j) {
         if (j < wg) {
           const float y = Ys[k * w + min(tt + 16 * j, w - 1)];
           v[0][j] = fmaf(a0, y, v[0][j]);
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kMaxP / 16; ++j) {
       const int t = tt + 16 * j;
       if (j < wg && t < w) {
         Vs[ti * (w + 1) + t] = v[0][j];
@@ -204,22 +204,22 @@ __global__ void __launch_bounds__(256) k_ritz(DevWork wk, int n, int K, int w, i
   }
   if (!last_block(&wk.counters[CNT_RITZ * 512])) return;
   // final reduction in block order
-  __shared__ double fin4[4 * kMaxW];
+  __shared__ double fin4[4 * kMaxP];
   reduce_partials(wk.ritz_part, gridDim.x, 4 * w, 4 * w, fin4);
-  __shared__ double fin[4 * kMaxW];
+  __shared__ double fin[4 * kMaxP];
   for (int t = tid; t < w; t += blockDim.x) {
     fin[t] = fin4[t];
-    fin[kMaxW + t] = fin4[w + t];
-    fin[2 * kMaxW + t] = fin4[2 * w + t];
-    fin[3 * kMaxW + t] = fin4[3 * w + t];
+    fin[kMaxP + t] = fin4[w + t];
+    fin[2 * kMaxP + t] = fin4[2 * w + t];
+    fin[3 * kMaxP + t] = fin4[3 * w + t];
   }
   __syncthreads();
-  __shared__ double rres[kMaxW];
+  __shared__ double rres[kMaxP];
   for (int t = tid; t < w; t += blockDim.x) {  // one column per thread
-    double vv = fin[2 * kMaxW + t];
-    double lam = vv > 0.0 ? fin[kMaxW + t] / vv : th[t];  // Rayleigh quotient (FP64 sums)
+    double vv = fin[2 * kMaxP + t];
+    double lam = vv > 0.0 ? fin[kMaxP + t] / vv : th[t];  // Rayleigh quotient (FP64 sums)
     wk.lam[nw][t] = lam;
-    wk.colsum[nw][t] = fin[3 * kMaxW + t];
+    wk.colsum[nw][t] = fin[3 * kMaxP + t];
     rres[t] = sqrt(fin[t] / (vv > 0.0 ? vv : 1.0));
   }
   for (int t = w + tid; t < wk.ldv; t += blockDim.x) {
@@ -720,7 +720,7 @@ static size_t rebuild_smem(int r) {
 }
 
 void init_pdhg_attributes() {
-  cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_smem(kMaxK, kMaxW));
+  cudaFuncSetAttribute(k_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ritz_smem(kMaxK, kMaxP));
   cudaFuncSetAttribute(k_rebuild, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rebuild_smem(kMaxR));
 }
 

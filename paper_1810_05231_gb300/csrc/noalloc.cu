@@ -99,7 +99,7 @@ int aproj_noalloc_device(const float* S, int n, int lds, int r, float* P, int ld
     K = n;
     s = 0;
   } else {
-    lanczos_dims(r, set, kMaxK, w, K, s);
+    lanczos_dims(r, set, kMaxK, kMaxW, w, K, s);  // this scratch layout holds blocks of up to kMaxW
     if (r > w - 4) {
       err = "rank too large for the Lanczos block (r <= 60)";
       return PROXSDP_ERR_UNSUPPORTED;

@@ -14,7 +14,15 @@ namespace psdp {
 
 constexpr int kMaxWindow = 1024;  // longest stall window l (Sec. 3.2)
 constexpr int kMaxK = 128;        // largest Rayleigh-Ritz basis (one-block eigensolver)
-constexpr int kMaxW = 64;         // largest Lanczos block width
+constexpr int kMaxW = 64;         // largest Krylov block width (products, orthogonalisation pieces)
+constexpr int kMaxP = 112;        // largest kept Ritz block the kernels hold (the restart vectors, r + guard)
+// Largest target rank on the Lanczos path: a kept block of r + 16 = 80 and an
+// expansion of 48 fill the 128-wide Rayleigh-Ritz basis.  Measured on
+// cold-start projections (100 restart cycles, tolerance 1e-6): r = 72 with
+// 8 guard vectors stays 2.4e-4 off, r = 80 with an expansion of 32 1.5e-3,
+// r >= 96 with 16 about 4e-2.
+constexpr int kMaxRankLanczos = 64;
+constexpr int kMaxRankFactored = 60;  // the factored operator holds at most 63 factors
 constexpr int kFullEigMax = 128;  // n up to which the projection uses the dense eigensolver
 constexpr int kTile = 64;         // rebuild tile edge
 constexpr int kRedSlots = 16;     // scalar reductions per kernel
@@ -159,6 +167,10 @@ size_t block_matvec_scratch_floats(int n, int k);
 size_t block_matvec_counters(int n, int k);
 void launch_random_block(float* Q, int ldq, int n, int col0, int k, unsigned long long seed,
                          cudaStream_t st);
+// Z (n x b, stride ldz) = columns (off + j) mod w of W (n x w, stride ldw),
+// off = (restart cycles so far) * b mod w, read from the control block.
+void launch_compress_block(const float* W, int ldw, int w, float* Z, int ldz, int b, int n, const Ctl* ctl,
+                           const int* skip, cudaStream_t st);
 // launchers (k_mv_tc.cu): the tensor-core block product; false (nothing
 // launched) when it does not apply
 bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw, int k,

@@ -229,7 +229,7 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   CKA(dalloc(*this, &Wk.flags, kMaxW));
   CKA(dalloc(*this, &Wk.Y, (size_t)kMaxK * kMaxK));
   CKA(dalloc(*this, &Wk.theta, kMaxK));
-  CKA(dalloc(*this, &Wk.ritz_part, ((size_t)(n + 31) / 32 + 1) * 4 * kMaxW));
+  CKA(dalloc(*this, &Wk.ritz_part, ((size_t)(n + 31) / 32 + 1) * 4 * kMaxP));
   CKA(dalloc(*this, &Wk.counters, (size_t)CNT_NUM * 512));
   CKA(dalloc(*this, &Wk.ctl, 1));
   CKA(dalloc(*this, &Vcm, (size_t)ld * 2 * kMaxR));
@@ -248,7 +248,7 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   saved_r = 0;
   saved_it = -1;
   saved_seen = 0;
-  CKA(dalloc(*this, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxW)));
+  CKA(dalloc(*this, &Wk.mv_part, block_matvec_scratch_floats(n, kMaxP)));  // the warm product has up to kMaxP columns
   CKA(dalloc(*this, &Wk.mv_cnt, block_matvec_counters(n, kMaxW)));
   CK(cudaMemsetAsync(Wk.mv_cnt, 0, sizeof(unsigned) * block_matvec_counters(n, kMaxW), st));
   CK(cudaMemsetAsync(Wk.counters, 0, sizeof(unsigned) * CNT_NUM * 512, st));
@@ -261,15 +261,31 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   return PROXSDP_OK;
 }
 
-void lanczos_dims(int rr, const proxsdp_gpu_settings& set, int k_target, int& w, int& K, int& s) {
+void lanczos_dims(int rr, const proxsdp_gpu_settings& set, int k_target, int wmax, int& w, int& K, int& s) {
   const int b = std::max(1, set.block_size);
   const int g = set.guard > 0 ? set.guard : std::max(8, rr / 4);
   w = ((rr + g + b - 1) / b) * b;
+  if (w > kMaxW && wmax > kMaxW) {
+    // wide kept block: r + 8 vectors (or r + guard when set), at most kMaxP,
+    // leaving the largest expansion of K - w <= kMaxW directions per cycle
+    const int gw = set.guard > 0 ? set.guard : 8;
+    w = std::min(((rr + gw + b - 1) / b) * b, kMaxP);
+    s = 1;
+    K = std::min(kMaxK, w + kMaxW);
+    return;
+  }
   w = std::min(w, kMaxW);
   if (set.lanczos_steps > 0) s = set.lanczos_steps;
   else s = std::max(1, k_target / w - 1);
   while ((s + 1) * w > kMaxK && s > 1) --s;
   K = (s + 1) * w;
+}
+
+int Solver::rank_cap() const {
+  const int n = hp.n;
+  if (set.full_eig) return n;
+  if (n <= kFullEigMax) return std::min(set.max_rank, n);
+  return std::min(std::min(set.max_rank, n), factored ? kMaxRankFactored : kMaxRankLanczos);
 }
 
 // Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s for rank r.
@@ -281,7 +297,7 @@ void Solver::dims(int rr, int& w, int& K, int& s) const {
     s = 0;
     return;
   }
-  lanczos_dims(rr, set, k_target, w, K, s);
+  lanczos_dims(rr, set, k_target, factored ? kMaxW : kMaxP, w, K, s);
 }
 
 int Solver::set_ctl_fields(int status, int it_stop, int rr, int w, int K, int k_change) {
@@ -320,8 +336,31 @@ void enqueue_orth(const DevWork& wk, int n, int c0, int w, unsigned long long se
   }
 }
 
-// One Cholesky-QR pass on Q[:, c0:c0+w] (re-orthonormalises the kept Ritz block).
+// Kernels enqueue_orth launches for Q[:, c0:c0+w] (with a source to copy from or not).
+static int orth_kernel_count(int n, int c0, int w, bool src) {
+  if (orth_cluster_applies(n, c0, w)) return 1;
+  return (src ? 1 : 0) + 2 * ((c0 > 0 ? 2 : 0) + 3);
+}
+
+// enqueue_orth for blocks wider than kMaxW: pieces of at most kMaxW columns,
+// each orthogonalised against everything before it.
+static void enqueue_orth_wide(const DevWork& wk, int n, int c0, int w, unsigned long long seed, const int* skip,
+                              cudaStream_t st) {
+  for (int off = 0; off < w; off += kMaxW)
+    enqueue_orth(wk, n, c0 + off, std::min(kMaxW, w - off), seed + (unsigned long long)off, skip, st);
+}
+
+static int cholqr_kernel_count(int n, int w);
+
+// One Cholesky-QR pass on Q[:, c0:c0+w] (re-orthonormalises the kept Ritz
+// block); a block wider than kMaxW is re-orthonormalised piece by piece.
 static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned long long seed, cudaStream_t st) {
+  if (w > kMaxW) {
+    enqueue_cholqr(wk, n, c0, kMaxW, seed, st);
+    for (int off = kMaxW; off < w; off += kMaxW)
+      enqueue_orth(wk, n, c0 + off, std::min(kMaxW, w - off), seed + (unsigned long long)off, nullptr, st);
+    return;
+  }
   float* Z = wk.Q + (size_t)c0 * wk.ldq;
   if (orth_cluster_applies(n, c0, w)) {
     launch_orth_cluster(wk.Q, wk.ldq, Z, n, c0, w, 1, 0, seed, nullptr, st);
@@ -333,10 +372,37 @@ static void enqueue_cholqr(const DevWork& wk, int n, int c0, int w, unsigned lon
   launch_apply_rinv(Z, wk.ldq, w, wk.Hf, wk.flags, n, seed, nullptr, st);
 }
 
+static int cholqr_kernel_count(int n, int w) {
+  if (w <= kMaxW) return orth_cluster_applies(n, 0, w) ? 1 : 3;
+  int c = cholqr_kernel_count(n, kMaxW);
+  for (int off = kMaxW; off < w; off += kMaxW) c += orth_kernel_count(n, off, std::min(kMaxW, w - off), false);
+  return c;
+}
+
 void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
                    unsigned long long seed, cudaGraphConditionalHandle cond, int use_cond,
                    cudaStream_t st, const DevProblem* fac) {
   const int* skip = &wk.ctl->lz_done;
+  if (w > kMaxW) {
+    // wide kept block: one expansion by bx = K - w residual directions of a
+    // window of the kept vectors that rotates with the cycles
+    // (k_compress_block), orthogonalised in place
+    const int bx = K - w;
+    float* Z = wk.Q + (size_t)w * wk.ldq;
+    float* W1 = wk.W + (size_t)w * wk.ldq;
+    launch_compress_block(wk.W, wk.ldq, w, Z, wk.ldq, bx, n, wk.ctl, skip, st);
+    enqueue_orth(wk, n, w, bx, seed + 1ULL, skip, st);
+    if (fac) launch_factored_matvec(*fac, wk, Z, wk.ldq, W1, wk.ldq, bx, skip, st);
+    else launch_block_matvec(wk.S, wk.lds, n, Z, wk.ldq, W1, wk.ldq, bx, skip, st, wk.mv_part, wk.mv_cnt);
+    dbg(wk, "wide cycle matvec", st);
+    launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
+    launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
+    const int launches = 4 + orth_kernel_count(n, w, bx, false) +
+                         (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
+    launch_ritz(wk, n, K, w, r, 1, launches, cond, use_cond, st);
+    dbg(wk, "ritz", st);
+    return;
+  }
   for (int j = 1; j <= s; ++j) {
     enqueue_orth(wk, n, j * w, w, seed + (unsigned long long)j, skip, st, wk.W + (size_t)(j - 1) * w * wk.ldq);
     const float* Qj = wk.Q + (size_t)j * w * wk.ldq;
@@ -351,7 +417,7 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
   dbg(wk, "rr eig", st);
   // Gram of T, eigensolver, Ritz; the products
   int cycle_launches = 3 + s * (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
-  for (int j = 1; j <= s; ++j) cycle_launches += orth_cluster_applies(n, j * w, w) ? 1 : 11;
+  for (int j = 1; j <= s; ++j) cycle_launches += orth_kernel_count(n, j * w, w, true);
   launch_ritz(wk, n, K, w, r, s, cycle_launches, cond, use_cond, st);
   dbg(wk, "ritz", st);
 }
@@ -368,7 +434,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   } else {
     if (g_debug) g_debug_n = n;
     enqueue_cholqr(wk, n, 0, k.w, seed + 17, st);
-    if (factored)
+    if (factored)  // the factored form keeps w <= kMaxW (rank cap)
       launch_factored_matvec(pb, wk, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, inner, use);
     else
       launch_block_matvec(wk.S, wk.lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, k.w, nullptr, st, wk.mv_part, wk.mv_cnt,
@@ -414,7 +480,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   // kernels per iteration outside the restart cycles: Cholesky-QR, the warm
   // product, M(X)/dual step, D values, Gram + controller, the rebuild of S
   const int iter_launches = k.full ? 7
-                                   : (orth_cluster_applies(n, 0, k.w) ? 1 : 3) +
+                                   : cholqr_kernel_count(n, k.w) +
                                          (factored ? kFactoredLaunches + 3
                                                    : 4 + block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
   launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
@@ -490,7 +556,7 @@ int Solver::init_iterate_zero() {
   saved_it = -1;
   saved_seen = 0;
   r = std::max(1, std::min(set.full_eig ? n : set.rank_init, n));
-  if (!set.full_eig) r = std::min(r, set.max_rank);
+  if (!set.full_eig) r = std::min(r, rank_cap());
   int w, K, s;
   dims(r, w, K, s);
   Ctl c;
@@ -504,7 +570,7 @@ int Solver::init_iterate_zero() {
   c.full_eig = set.full_eig ? 1 : 0;
   c.full_eig_path = (n <= kFullEigMax || set.full_eig) ? 1 : 0;
   c.window = std::max(1, std::min(set.window, kMaxWindow));
-  c.max_rank = set.full_eig ? n : std::min(set.max_rank, n);
+  c.max_rank = rank_cap();
   c.max_cycles = std::max(1, set.lanczos_max_cycles);
   c.tol = set.tol;
   c.eps_lambda = set.eps_lambda > 0 ? set.eps_lambda : set.tol;
@@ -518,7 +584,7 @@ int Solver::init_iterate_zero() {
   if (!factored) launch_rebuild(pb, wk, 1, 0, st);
   if (!(n <= kFullEigMax || set.full_eig)) {
     launch_random_block(wk.Q, wk.ldq, n, 0, w, seed, st);
-    enqueue_orth(wk, n, 0, w, seed, nullptr, st);
+    enqueue_orth_wide(wk, n, 0, w, seed, nullptr, st);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -531,7 +597,7 @@ int Solver::init_iterate_zero() {
 int Solver::grow_basis(int w_old, int w_new) {
   if (w_new <= w_old || hp.n <= kFullEigMax || set.full_eig) return PROXSDP_OK;
   launch_random_block(wk.Q, wk.ldq, hp.n, w_old, w_new - w_old, seed + 31ULL * (unsigned long long)w_new, st);
-  enqueue_orth(wk, hp.n, w_old, w_new - w_old, seed + 7ULL * (unsigned long long)w_new, nullptr, st);
+  enqueue_orth_wide(wk, hp.n, w_old, w_new - w_old, seed + 7ULL * (unsigned long long)w_new, nullptr, st);
   CK(cudaGetLastError());
   return PROXSDP_OK;
 }
@@ -618,7 +684,7 @@ int Solver::run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info
       continue;
     }
     if (status == ST_RANK_CHANGE) {
-      int r_new = std::min(std::min(2 * r, n), std::max(set.max_rank, 1));
+      int r_new = std::min(2 * r, std::max(rank_cap(), 1));
       int w_old = w;
       r = r_new;
       int w2, K2, s2;
@@ -727,7 +793,7 @@ int Solver::set_iterate(int rr, const double* V, const double* lam, const double
   c->it = 0;
   c->k_change = 0;
   c->status = ST_RUNNING;
-  c->max_rank = set.full_eig ? n : std::min(std::max(set.max_rank, rr), n);
+  c->max_rank = std::max(rank_cap(), rr);
   CK(cudaMemcpyAsync(wk.ctl, c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
   // S^k = X^k - alpha (C + M*(y^k)), Lanczos warm start = the given factors
   launch_dvals(pb, wk, st);
@@ -737,7 +803,7 @@ int Solver::set_iterate(int rr, const double* V, const double* lam, const double
                        cudaMemcpyHostToDevice, st));
     if (w > rr) {
       launch_random_block(wk.Q, wk.ldq, n, rr, w - rr, seed + 5, st);
-      enqueue_orth(wk, n, rr, w - rr, seed + 9, nullptr, st);
+      enqueue_orth_wide(wk, n, rr, w - rr, seed + 9, nullptr, st);
     }
   }
   CK(cudaGetLastError());
@@ -785,8 +851,8 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
   sv.r = r;
   int w, K, s;
   sv.dims(r, w, K, s);
-  if (!full && r > w - 4) {
-    err = "rank too large for the Lanczos block (r <= 60)";
+  if (!full && r > std::min(w - 4, kMaxRankLanczos)) {
+    err = "rank too large for the Lanczos block (r <= 64)";
     return PROXSDP_ERR_UNSUPPORTED;
   }
   Ctl c;
@@ -813,7 +879,7 @@ int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float
     launch_full_eig_factors(wk, n, sv.st);
   } else {
     launch_random_block(wk.Q, wk.ldq, n, 0, w, sv.seed, sv.st);
-    enqueue_orth(wk, n, 0, w, sv.seed, nullptr, sv.st);
+    enqueue_orth_wide(wk, n, 0, w, sv.seed, nullptr, sv.st);
     launch_block_matvec(S, lds, n, wk.Q, wk.ldq, wk.W, wk.ldq, w, nullptr, sv.st, wk.mv_part, wk.mv_cnt);
     for (int cyc = 0; cyc < c.max_cycles; ++cyc)
       enqueue_cycle(wk, n, w, K, s, r, sv.seed + 1000ULL * (unsigned long long)(cyc + 1), 0, 0, sv.st);

@@ -81,6 +81,9 @@ struct Solver {
   int run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info);
   int read_ctl();
   void dims(int r, int& w, int& K, int& s) const;
+  // largest target rank of this handle: max_rank, n, and on the Lanczos path
+  // kMaxRankLanczos (kMaxRankFactored with the factored operator)
+  int rank_cap() const;
   int grow_basis(int w_old, int w_new);
   int enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditionalHandle outer,
                         cudaGraphConditionalHandle inner);
@@ -95,11 +98,14 @@ struct Solver {
 int check_settings(const proxsdp_gpu_settings& s, std::string& err);
 int check_device(int device, std::string& err);
 
-// Krylov block width w, Rayleigh-Ritz basis K = (s+1) w and steps s per
-// restart cycle for target rank r on the block Lanczos path (n > kFullEigMax):
-// w = the smallest multiple of block_size holding r + guard vectors (at most
-// kMaxW), s = k_target / w - 1 steps unless lanczos_steps fixes it, K <= kMaxK.
-void lanczos_dims(int r, const proxsdp_gpu_settings& set, int k_target, int& w, int& K, int& s);
+// Kept Ritz block w, Rayleigh-Ritz basis K and Krylov steps s per restart
+// cycle for target rank r on the block Lanczos path (n > kFullEigMax):
+// w = the smallest multiple of block_size holding r + guard vectors.  Up to
+// kMaxW the kept block is also the Krylov block: s = k_target / w - 1 steps
+// unless lanczos_steps fixes it, K = (s + 1) w <= kMaxK.  Beyond kMaxW (when
+// wmax allows it) the kept block holds up to kMaxP vectors (at least r + 8)
+// and one cycle expands it by K - w <= kMaxW directions, K <= kMaxK.
+void lanczos_dims(int r, const proxsdp_gpu_settings& set, int k_target, int wmax, int& w, int& K, int& s);
 
 // device helpers used by the API (solver.cu)
 int aproj_device(const float* S, int n, int lds, int r, float* P, int ldp, float* V, double* lambda,

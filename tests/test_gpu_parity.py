@@ -92,7 +92,7 @@ def _spectrum(n, npos, seed, gap=0.3):
 
 @pytest.mark.parametrize("n,r,npos", [(50, 5, 10), (127, 8, 8), (129, 8, 20), (300, 8, 30), (777, 16, 24),
                                       (1000, 32, 40), (2000, 8, 12), (2000, 16, 64), (2000, 60, 70),
-                                      (5000, 16, 24)])
+                                      (5000, 16, 24), (2000, 64, 80), (3000, 64, 80)])
 def test_aproj_known_spectrum(pkg, n, r, npos):
     lam = _spectrum(n, npos, seed=n + r)
     # separate lambda_r from lambda_{r+1} by a relative gap so the truncation is unique
@@ -130,7 +130,7 @@ def _shared_iterate(inst, r, iters):
 
 @pytest.mark.parametrize("form", [0, 1], ids=["explicit", "factored"])
 @pytest.mark.parametrize("kind,n,r", [("maxcut", 200, 4), ("maxcut", 90, 6), ("equi", 160, 8), ("sensor", 0, 8),
-                                      ("workload", 2000, 16)])
+                                      ("workload", 2000, 16), ("maxcut", 400, 64)])
 def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
     """form 1 applies S^k from the factors of X^k (n > 128; n = 90 takes the
     dense eigensolver, which always forms S)."""
@@ -148,6 +148,13 @@ def test_one_iteration_matches_oracle(pkg, kind, n, r, form):
     sp, scale = normalize_rows(prob)
     slv = pkg.Solver(rank_init=r, max_rank=r, lanczos_tol=1e-6, lanczos_max_cycles=30, operator_form=form)
     slv.set_instance(inst)
+    if form == 1 and r > 60:
+        # the factored operator holds at most 60 factors: rejected, not run
+        with pytest.raises(pkg.ProxSDPError) as e:
+            slv.set_iterate(Vx, lx, yp)
+        assert e.value.code == pkg.ERR_UNSUPPORTED
+        slv.close()
+        return
     slv.set_iterate(Vx, lx, yp)
     info = slv.iterate(1)
     got = slv.get_primal_dual()
