@@ -225,6 +225,19 @@ int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const doubl
  * rule active), then fill `info` with the residuals of the last one. */
 int proxsdp_gpu_iterate(proxsdp_gpu_t h, int64_t iters, proxsdp_gpu_info* info);
 
+/* Continue Alg. 2 from the current iterate until its stop test holds (Sec. 3.2:
+ * residuals within the tolerance at a sufficient rank, gap within the
+ * tolerance), for at most `max_iters` further iterations (< 0: up to
+ * settings.max_iter in total) and settings.time_limit_s for this call.  The
+ * current iterate is where the last solve, iterate or resume call stopped,
+ * or the one given to proxsdp_gpu_set_iterate (for instance a saved feasible
+ * pair (X_[r], y_[r]) from proxsdp_gpu_get_saved_pair); without one the run
+ * starts from X = 0, y = 0 like proxsdp_gpu_solve.  Iteration counts in
+ * `info` are cumulative.  A solve interrupted by a cap and resumed goes
+ * through the same iterates as one run without interruption.  Returns
+ * PROXSDP_ERR_BAD_STATE before set_problem. */
+int proxsdp_gpu_resume(proxsdp_gpu_t h, int64_t max_iters, proxsdp_gpu_info* info);
+
 /* Destroy the handle and free its device memory. */
 void proxsdp_gpu_destroy(proxsdp_gpu_t h);
 

@@ -42,6 +42,7 @@ EXPORTED = [
     "proxsdp_gpu_get_saved_pair",
     "proxsdp_gpu_set_iterate",
     "proxsdp_gpu_iterate",
+    "proxsdp_gpu_resume",
     "proxsdp_gpu_destroy",
     "proxsdp_gpu_last_error",
     "proxsdp_gpu_aproj",
@@ -128,6 +129,7 @@ def lib():
     L.proxsdp_gpu_get_saved_pair.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.proxsdp_gpu_set_iterate.argtypes = [vp, i32, dp, dp, dp]
     L.proxsdp_gpu_iterate.argtypes = [vp, i64, ctypes.POINTER(Info)]
+    L.proxsdp_gpu_resume.argtypes = [vp, i64, ctypes.POINTER(Info)]
     L.proxsdp_gpu_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Info), i32]
     L.proxsdp_gpu_destroy.argtypes = [vp]
     L.proxsdp_gpu_destroy.restype = None
@@ -232,6 +234,13 @@ class Solver:
     def iterate(self, iters: int) -> Info:
         info = Info()
         _check(lib().proxsdp_gpu_iterate(self.h, int(iters), ctypes.byref(info)), self.h)
+        return info
+
+    def resume(self, max_iters: int = -1) -> Info:
+        """Continue Alg. 2 from the current iterate until its stop test holds
+        (at most ``max_iters`` more iterations; < 0: up to ``max_iter`` in total)."""
+        info = Info()
+        _check(lib().proxsdp_gpu_resume(self.h, int(max_iters), ctypes.byref(info)), self.h)
         return info
 
     def set_iterate(self, V, lam, y=None):

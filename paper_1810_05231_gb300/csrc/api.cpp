@@ -574,6 +574,18 @@ int proxsdp_gpu_iterate(proxsdp_gpu_t h, int64_t iters, proxsdp_gpu_info* info) 
   return S.run(iters, false, info);
 }
 
+int proxsdp_gpu_resume(proxsdp_gpu_t h, int64_t max_iters, proxsdp_gpu_info* info) {
+  if (!h) return PROXSDP_ERR_INVALID_ARG;
+  Solver& S = h->s;
+  if (!S.has_problem) return S.fail(PROXSDP_ERR_BAD_STATE, "resume before set_problem");
+  cudaSetDevice(S.device);
+  if (!S.has_iterate) {
+    int rc = S.init_iterate_zero();
+    if (rc) return rc;
+  }
+  return S.run(max_iters < 0 ? -1 : max_iters, true, info);
+}
+
 int proxsdp_gpu_set_iterate(proxsdp_gpu_t h, int r, const double* V, const double* lambda,
                             const double* y) {
   if (!h) return PROXSDP_ERR_INVALID_ARG;

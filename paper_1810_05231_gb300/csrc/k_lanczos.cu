@@ -682,12 +682,14 @@ __device__ void tri_lu(const float* d, const float* e, int K, float lam, float t
   f.u0[K - 1] = 1.f / ((p0 == 0.f) ? tiny : p0);
 }
 
-// x <- (T - lam I)^{-1} x for the factorisation above; x has stride ld.
+// x <- (T - lam I)^{-1} x for the factorisation above; x has stride ld > 0
+// (loads of x issued one step ahead of the store before them).
 __device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
   float a = x[0];  // the current row's entry, carried in a register
-#pragma unroll 4
+  float bn = (K > 1) ? x[ld] : 0.f;
   for (int i = 0; i < K - 1; ++i) {
-    float b = x[(i + 1) * ld];
+    float b = bn;
+    if (i + 2 < K) bn = x[(i + 2) * ld];
     if ((f.sw[i >> 5] >> (i & 31)) & 1u) {
       const float t = a;
       a = b;
@@ -697,10 +699,12 @@ __device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
     a = fmaf(-f.l[i], a, b);
   }
   float x2 = 0.f, x1 = a * f.u0[K - 1];
+  float xn = (K > 1) ? x[(K - 2) * ld] : 0.f;
   x[(K - 1) * ld] = x1;
-#pragma unroll 4
   for (int i = K - 2; i >= 0; --i) {
-    const float xi = (x[i * ld] - f.u1[i] * x1 - f.u2[i] * x2) * f.u0[i];
+    const float xv = xn;
+    if (i > 0) xn = x[(i - 1) * ld];
+    const float xi = (xv - f.u1[i] * x1 - f.u2[i] * x2) * f.u0[i];
     x[i * ld] = xi;
     x2 = x1;
     x1 = xi;
@@ -714,8 +718,9 @@ __device__ void tri_solve(const TriLU& f, int K, float* x, int ld) {
 // (e_i, d_{i+1} - lam, e_{i+1}); an unswapped row is (p0_i, p1_i, 0) with
 // p1_i = e_i after an unswapped row (or at i = 0) and -l_{i-1} e_i after a
 // swapped one.
-__device__ void tri_lu_slot(const float* d, const float* e, int K, float lam, float tiny, float* lm, float* rp,
-                            unsigned* sw, int ns, int s) {
+__device__ void tri_lu_slot(const float* __restrict__ d, const float* __restrict__ e, int K, float lam, float tiny,
+                            float* __restrict__ lm, float* __restrict__ rp, unsigned* __restrict__ sw, int ns,
+                            int s) {
   float p0 = d[0] - lam, p1 = (K > 1) ? e[0] : 0.f;
   for (int w = 0; w < (K + 31) / 32; ++w) sw[w * ns + s] = 0u;
   unsigned bits = 0u;
@@ -746,12 +751,17 @@ __device__ void tri_lu_slot(const float* d, const float* e, int K, float lam, fl
   rp[(K - 1) * ns + s] = __frcp_rn((p0 == 0.f) ? tiny : p0);
 }
 
-__device__ void tri_solve_slot(const float* d, const float* e, int K, float lam, const float* lm, const float* rp,
-                               const unsigned* sw, int ns, int s, float* x, int ld) {
+// x holds the right-hand side on entry (stride ld > 0) and the solution on
+// exit.  Every load of x is issued one step ahead of the store before it (the
+// entries differ), which keeps the memory latency off the recurrence.
+__device__ void tri_solve_slot(const float* __restrict__ d, const float* __restrict__ e, int K, float lam,
+                               const float* __restrict__ lm, const float* __restrict__ rp,
+                               const unsigned* __restrict__ sw, int ns, int s, float* x, int ld) {
   float a = x[0];
-#pragma unroll 4
+  float bn = (K > 1) ? x[ld] : 0.f;
   for (int i = 0; i < K - 1; ++i) {
-    float b = x[(i + 1) * ld];
+    float b = bn;
+    if (i + 2 < K) bn = x[(i + 2) * ld];
     if ((sw[(i >> 5) * ns + s] >> (i & 31)) & 1u) {
       const float t = a;
       a = b;
@@ -761,8 +771,11 @@ __device__ void tri_solve_slot(const float* d, const float* e, int K, float lam,
     a = fmaf(-lm[i * ns + s], a, b);
   }
   float x2 = 0.f, x1 = a * rp[(K - 1) * ns + s];
+  float xn = (K > 1) ? x[(K - 2) * ld] : 0.f;
   x[(K - 1) * ld] = x1;
   for (int i = K - 2; i >= 0; --i) {
+    const float xv = xn;
+    if (i > 0) xn = x[(i - 1) * ld];
     const bool swp = (sw[(i >> 5) * ns + s] >> (i & 31)) & 1u;
     float u1, u2;
     if (swp) {
@@ -773,7 +786,7 @@ __device__ void tri_solve_slot(const float* d, const float* e, int K, float lam,
       u1 = prev_swp ? -lm[(i - 1) * ns + s] * e[i] : e[i];
       u2 = 0.f;
     }
-    const float xi = (x[i * ld] - u1 * x1 - u2 * x2) * rp[i * ns + s];
+    const float xi = (xv - u1 * x1 - u2 * x2) * rp[i * ns + s];
     x[i * ld] = xi;
     x2 = x1;
     x1 = xi;
@@ -1109,12 +1122,15 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
     s_ng = ng;
   }
   __syncthreads();
-  {  // isolated eigenvalues: one thread each, two solves (each multiplies the
-     // wanted component by at least gap / |lambda error| > 100 against any
-     // other: eigenvalues closer than kSeGroupTol go to the group path); LU factors in
-     // shared-memory slots (the refinement scratch), in batches of ns
-    const int nwords = (K + 31) / 32;
-    const int ns = min(nth, (int)((Kp * (Kp + 1) / 2 + 2 * Kp * JB) / (2 * K + nwords)));
+  // isolated eigenvalues: one thread each, two solves (each multiplies the
+  // wanted component by at least gap / |lambda error| > 100 against any
+  // other: eigenvalues closer than kSeGroupTol go to the group path); LU
+  // factors in shared-memory slots (the refinement scratch), in batches of ns.
+  // The groups go to the warps that hold no isolated slot.
+  const int nwords = (K + 31) / 32;
+  const int ns = min(nth, (int)((Kp * (Kp + 1) / 2 + 2 * Kp * JB) / (2 * K + nwords)));
+  const int wbusy = min(nwarps - 1, (min(ns, K - a_need) + 31) / 32);
+  {
     float* lm = scr;
     float* rp = lm + (size_t)K * ns;
     unsigned* swb = reinterpret_cast<unsigned*>(rp + (size_t)K * ns);
@@ -1139,17 +1155,20 @@ __global__ void __launch_bounds__(SE_THREADS) k_sym_eig(const double* __restrict
 #pragma unroll 4
           for (int i = 0; i < K; ++i) {
             const float v = x[i * ld] * im;
-            x[i * ld] = v;
             ss = fmaf(v, v, ss);
           }
           const float is = rsqrtf(ss);
-#pragma unroll 4
-          for (int i = 0; i < K; ++i) x[i * ld] *= is;
+          float xn = x[0];
+          for (int i = 0; i < K; ++i) {
+            const float xv = xn;
+            if (i + 1 < K) xn = x[(i + 1) * ld];
+            x[i * ld] = (xv * im) * is;
+          }
         }
       }
     }
   }
-  for (int gi = warp; gi < s_ng; gi += nwarps) {  // groups: lane = member, MGS in member order
+  for (int gi = warp - wbusy; warp >= wbusy && gi < s_ng; gi += nwarps - wbusy) {  // groups: lane = member, MGS in member order
     const int a0 = glist[gi], c = gsz[a0];
     for (int base = a0; base < a0 + c; base += 32) {
       const int cc = min(32, a0 + c - base);

@@ -82,6 +82,26 @@ def test_sym_eig(pkg, K):
     assert np.linalg.norm(Yn.T @ Yn - np.eye(K)) <= 1e-5 * math.sqrt(K)
 
 
+@pytest.mark.parametrize("K", [32, 96, 128])
+def test_sym_eig_ritz_values_fp64_grade(pkg, K):
+    """The Rayleigh-Ritz eigensolve runs in FP32 with the FP32-pair refinement
+    (Ogita-Aishima step, T y accumulated in FP32 pairs against the FP64 T,
+    Rayleigh quotients in FP64): on a separated spectrum the Ritz values
+    reach FP64 grade (<= 1e-11 ||T||) while the vectors stay FP32 grade."""
+    rng = np.random.default_rng(100 + K)
+    lam = np.sort(np.linspace(-1.0, 1.0, K) + rng.uniform(-0.2, 0.2, K) / K)[::-1] * 7.0
+    Q, _ = np.linalg.qr(rng.standard_normal((K, K)))
+    T = (Q * lam) @ Q.T
+    T = (T + T.T) / 2
+    theta, Y = pkg.sym_eig(torch.tensor(T, device=DEV))
+    torch.cuda.synchronize()
+    th = theta.cpu().numpy()
+    Yn = Y.double().cpu().numpy()
+    nT = np.abs(lam).max()
+    assert np.max(np.abs(th - lam)) <= 1e-11 * nT, np.max(np.abs(th - lam)) / nT
+    assert np.linalg.norm(T @ Yn - Yn * th, axis=0).max() <= 2e-6 * nT
+
+
 def _spectrum(n, npos, seed, gap=0.3):
     rng = np.random.default_rng(seed)
     pos = np.sort(rng.uniform(1.0, 10.0, npos))[::-1]

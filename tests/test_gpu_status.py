@@ -152,3 +152,68 @@ def test_saved_feasible_pair(pkg, n):
     assert e.value.code == pkg.ERR_BAD_STATE
     slv.close()
     slv2.close()
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_resume_after_interruption_follows_the_same_iterates(pkg, graphs):
+    """An Alg. 2 run stopped after a fixed number of iterations and resumed
+    reaches the stop test at the same iteration, rank and objective as the
+    run without interruption (the iteration state stays on the device)."""
+    inst = si.maxcut_er(300, 0.03, 2)
+    ref = pkg.Solver(tol=1e-4, rank_init=2, check_every=10, use_graphs=graphs)
+    ref.set_instance(inst)
+    a = ref.solve()
+    assert a.status == pkg.CONVERGED, a.as_dict()
+    assert a.iters > 60
+    slv = pkg.Solver(tol=1e-4, rank_init=2, check_every=10, use_graphs=graphs)
+    slv.set_instance(inst)
+    part = slv.iterate(a.iters // 3 + 7)
+    assert part.status == pkg.MAX_ITER and part.iters == a.iters // 3 + 7
+    b = slv.resume(5)  # a budget of five more iterations
+    assert b.status == pkg.MAX_ITER and b.iters == part.iters + 5
+    b = slv.resume()
+    assert b.status == pkg.CONVERGED, b.as_dict()
+    assert (b.iters, b.final_rank) == (a.iters, a.final_rank)
+    assert b.primal_obj == a.primal_obj and b.dual_obj == a.dual_obj
+    got, want = slv.get_primal_dual(), ref.get_primal_dual()
+    np.testing.assert_array_equal(got["X"], want["X"])
+    np.testing.assert_array_equal(got["y"], want["y"])
+    # a converged iterate resumes to the stop test at once
+    c = slv.resume()
+    assert c.status == pkg.CONVERGED and c.iters - b.iters <= 1
+    ref.close()
+    slv.close()
+
+
+@pytest.mark.parametrize("kind", ["dense_path", "lanczos_path"])
+def test_resume_from_saved_pair(pkg, kind):
+    """Restart Alg. 2 from its saved feasible pair (X_[r], y_[r]) of Sec. 3.2
+    on a fresh handle: the run reaches the stop test at the optimum of the
+    uninterrupted solve (objective within 1e-4, certificates at 1e-4)."""
+    inst = _complete(16) if kind == "dense_path" else si.maxcut_er(300, 0.03, 2)
+    slv = pkg.Solver(tol=1e-6, rank_init=1)
+    slv.set_instance(inst)
+    a = slv.solve()
+    assert a.status == pkg.CONVERGED, a.as_dict()
+    sv = slv.get_saved_pair()
+    assert sv["r"] < a.final_rank
+    res = pkg.Solver(tol=1e-6, rank_init=1)
+    res.set_instance(inst)
+    res.set_iterate(sv["V"], sv["lam"], sv["y"])
+    b = res.resume()
+    assert b.status == pkg.CONVERGED, b.as_dict()
+    assert b.final_rank >= a.final_rank // 2
+    assert abs(b.primal_obj - a.primal_obj) <= 1e-4 * (1 + abs(a.primal_obj)), (a.primal_obj, b.primal_obj)
+    got = res.get_primal_dual()
+    cert = oracle.certificates(Problem.from_instance(inst), got["X"], -got["y"])
+    assert cert["primal_eq"] <= 1e-4 and cert["rel_gap"] <= 1e-4, cert
+    slv.close()
+    res.close()
+
+
+def test_resume_before_problem_is_bad_state(pkg):
+    slv = pkg.Solver()
+    with pytest.raises(pkg.ProxSDPError) as e:
+        slv.resume()
+    assert e.value.code == pkg.ERR_BAD_STATE
+    slv.close()
