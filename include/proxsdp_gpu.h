@@ -201,6 +201,30 @@ int proxsdp_gpu_solve_batch(proxsdp_gpu_t* handles, int count, proxsdp_gpu_info*
 int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V,
                                 double* lambda, int64_t* r_out);
 
+/* Add the element-wise box -u <= X_ij <= u for all i != j (the bounds of the
+ * MIMO relaxation, Sec. 5.3) to the loaded problem as a structured class of
+ * n (n - 1) inequality rows, X_ij <= u and -X_ij <= u for i < j, without
+ * passing them as CSR rows: their duals are two dense n x n arrays on the
+ * device (8 n^2 bytes) and their dual step runs element-wise beside the
+ * rebuild of S^k.  The rows take part in everything the CSR rows do (the
+ * step alpha = alpha_frac / ||M||_2 of the extended operator, the residuals,
+ * rhs^T y), with the same row scaling (sqrt(2) when normalize_rows).  Call it
+ * after set_problem and before solve; a new set_problem removes it.
+ * Supported when every CSR row acts on the diagonal only (diag(X) = b type
+ * rows, as in Sec. 5.3) and the operator form is explicit: otherwise
+ * PROXSDP_ERR_UNSUPPORTED (pass the bounds as CSR rows instead).
+ * PROXSDP_ERR_INVALID_ARG unless 0 < u < inf; PROXSDP_ERR_BAD_STATE before
+ * set_problem. */
+int proxsdp_gpu_set_box(proxsdp_gpu_t h, double u);
+
+/* Copy the duals of the element-wise box rows of the current iterate: n x n
+ * row-major, Y_upper for X_ij <= u and Y_lower for -X_ij <= u (i != j; zero
+ * diagonal), the paper's sign (<= 0) and original scaling, symmetric.
+ * Either pointer may be NULL.  PROXSDP_ERR_BAD_STATE without a box or an
+ * iterate.  proxsdp_gpu_set_iterate (and so a resume from a saved pair)
+ * starts the box duals from zero. */
+int proxsdp_gpu_get_box_dual(proxsdp_gpu_t h, double* Y_upper, double* Y_lower);
+
 /* Copy the feasible pair (X_[r], y_[r]) that Alg. 2 saves ("save feasible
  * solution", Sec. 3.2): the last iterate of the most recent solve / iterate
  * call at which the relative residuals met tol while the rank test found the

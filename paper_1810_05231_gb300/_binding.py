@@ -43,6 +43,8 @@ EXPORTED = [
     "proxsdp_gpu_set_iterate",
     "proxsdp_gpu_iterate",
     "proxsdp_gpu_resume",
+    "proxsdp_gpu_set_box",
+    "proxsdp_gpu_get_box_dual",
     "proxsdp_gpu_destroy",
     "proxsdp_gpu_last_error",
     "proxsdp_gpu_aproj",
@@ -130,6 +132,8 @@ def lib():
     L.proxsdp_gpu_set_iterate.argtypes = [vp, i32, dp, dp, dp]
     L.proxsdp_gpu_iterate.argtypes = [vp, i64, ctypes.POINTER(Info)]
     L.proxsdp_gpu_resume.argtypes = [vp, i64, ctypes.POINTER(Info)]
+    L.proxsdp_gpu_set_box.argtypes = [vp, ctypes.c_double]
+    L.proxsdp_gpu_get_box_dual.argtypes = [vp, dp, dp]
     L.proxsdp_gpu_solve_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Info), i32]
     L.proxsdp_gpu_destroy.argtypes = [vp]
     L.proxsdp_gpu_destroy.restype = None
@@ -242,6 +246,17 @@ class Solver:
         info = Info()
         _check(lib().proxsdp_gpu_resume(self.h, int(max_iters), ctypes.byref(info)), self.h)
         return info
+
+    def set_box(self, u: float = 1.0):
+        """Add -u <= X_ij <= u (i != j) as the structured element-wise box rows."""
+        _check(lib().proxsdp_gpu_set_box(self.h, float(u)), self.h)
+
+    def get_box_dual(self):
+        """Duals (paper's sign, original scaling) of X_ij <= u and -X_ij <= u, n x n each."""
+        n = self.n
+        Yu, Yl = np.empty((n, n)), np.empty((n, n))
+        _check(lib().proxsdp_gpu_get_box_dual(self.h, _ptr(Yu), _ptr(Yl)), self.h)
+        return Yu, Yl
 
     def set_iterate(self, V, lam, y=None):
         V = np.asfortranarray(V, dtype=np.float64)

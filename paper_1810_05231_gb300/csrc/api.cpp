@@ -660,6 +660,37 @@ int proxsdp_gpu_get_primal_dual(proxsdp_gpu_t h, double* X, double* y, double* V
   return PROXSDP_OK;
 }
 
+int proxsdp_gpu_set_box(proxsdp_gpu_t h, double u) {
+  if (!h) return PROXSDP_ERR_INVALID_ARG;
+  Solver& S = h->s;
+  cudaSetDevice(S.device);
+  return S.set_box(u);
+}
+
+int proxsdp_gpu_get_box_dual(proxsdp_gpu_t h, double* Y_upper, double* Y_lower) {
+  if (!h) return PROXSDP_ERR_INVALID_ARG;
+  Solver& S = h->s;
+  if (!S.has_problem || !S.has_iterate) return S.fail(PROXSDP_ERR_BAD_STATE, "no iterate yet");
+  if (!S.pb.box) return S.fail(PROXSDP_ERR_BAD_STATE, "no element-wise box was set");
+  cudaSetDevice(S.device);
+  const int n = S.hp.n, ld = S.wk.lds;
+  std::vector<float> buf((size_t)n * ld);
+  // paper's sign (<= 0), original scaling: y = -s y_scaled
+  const double sc = -(double)S.pb.box_s;
+  float* src[2] = {S.wk.ybp, S.wk.ybm};
+  double* dst[2] = {Y_upper, Y_lower};
+  for (int k = 0; k < 2; ++k) {
+    if (!dst[k]) continue;
+    if (cudaMemcpyAsync(buf.data(), src[k], sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, S.st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(S.st) != cudaSuccess)
+      return S.fail(PROXSDP_ERR_CUDA, "copy of the box duals failed");
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) dst[k][(size_t)i * n + j] = (i == j) ? 0.0 : sc * (double)buf[(size_t)i * ld + j];
+  }
+  return PROXSDP_OK;
+}
+
 int proxsdp_gpu_get_saved_pair(proxsdp_gpu_t h, double* X, double* y, double* V, double* lambda,
                                int64_t* r_out, int64_t* iter_out) {
   if (!h) return PROXSDP_ERR_INVALID_ARG;

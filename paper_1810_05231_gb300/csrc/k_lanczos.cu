@@ -19,6 +19,23 @@
 
 namespace psdp {
 
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
@@ -239,7 +256,8 @@ static int g_mv_cluster_max = 8;  // 16 where the device co-schedules 16-CTA clu
 static int matvec_slices(int n, int k) {
   const int tiles = ((n + MV_RB - 1) / MV_RB) * ((k + 63) / 64);
   int ns = 1;
-  while (ns < g_mv_cluster_max && tiles * (2 * ns) <= 304 && n >= (2 * ns) * 2 * MV_KC) ns *= 2;
+  const int slots = 2 * num_sms();  // two CTAs per SM
+  while (ns < g_mv_cluster_max && tiles * (2 * ns) <= slots && n >= (2 * ns) * 2 * MV_KC) ns *= 2;
   return ns;
 }
 
@@ -420,9 +438,10 @@ void launch_gram(const float* A, int lda, int ka, const float* B, int ldb, int k
     int per = (act + GR_T - 1) / GR_T;
     tiles = per * (ka / slot) * per * (kb / slot);
   }
-  // row splits: a power of two <= 8, >= 256 rows each, about 148 CTAs in all
+  // row splits: a power of two <= 8, >= 256 rows each, about one CTA per SM in all
   int ns = 1;
-  while (ns < 8 && tiles * ns * 2 <= 148 && n >= 2 * ns * 256) ns *= 2;
+  const int sms = num_sms();
+  while (ns < 8 && tiles * ns * 2 <= sms && n >= 2 * ns * 256) ns *= 2;
   const int rows = (n + ns - 1) / ns;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(tiles, ns, 1);

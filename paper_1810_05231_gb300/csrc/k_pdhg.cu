@@ -427,15 +427,16 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
   const double alpha = pb.alpha;
   const double x1 = v[0], x0 = v[1], x10 = v[2];
   const double dX2 = fmax(x1 + x0 - 2.0 * x10, 0.0);
-  const double ed2 = ctl->red_dual[0];
-  const double cross = ctl->red_dual[1];
-  const double ms2 = ctl->red_dvals[0];
+  // CSR rows plus the element-wise box rows (zero slots without a box)
+  const double ed2 = ctl->red_dual[0] + ctl->red_dvals[kRedBox];
+  const double cross = ctl->red_dual[1] + ctl->red_dvals[kRedBox + 1];
+  const double ms2 = ctl->red_dvals[0] + ctl->red_dvals[kRedBox + 3];
   // ||dX/alpha - M*(dy)||^2 = ||dX||^2/alpha^2 - 2/alpha <dX, M*(dy)> + ||M*(dy)||^2
   const double ep2 = dX2 / (alpha * alpha) - 2.0 * cross / alpha + ms2;
   const double eps_p = sqrt(fmax(ep2, 0.0));
   const double eps_d = sqrt(fmax(ed2, 0.0));
   const double pobj = ctl->red_dual[3];
-  const double dobj = -ctl->red_dual[2];
+  const double dobj = -(ctl->red_dual[2] + ctl->red_dvals[kRedBox + 2]);
   const double rel_p = eps_p / (1.0 + pb.normC);
   const double rel_d = eps_d / (1.0 + pb.normRhs);
   const double rel_gap = fabs(pobj - dobj) / (1.0 + fabs(pobj) + fabs(dobj));
@@ -630,9 +631,148 @@ __global__ void __launch_bounds__(256) k_rebuild(DevProblem pb, DevWork wk, int 
     Tl[(loc / kTile) * (kTile + 1) + loc % kTile] -= (float)(pb.alpha * wk.D[pb.tile_u[e]]);
   }
   __syncthreads();
+  // element-wise box rows: M*(y) holds box_s (y_up - y_lo) / 2 off the diagonal
+  const float abox = (float)(pb.alpha * 0.5 * (double)pb.box_s);
   for (int idx = tid; idx < kTile * kTile; idx += blockDim.x) {
     int i = idx / kTile, j = idx % kTile;
-    if (p0 + i < n && q0 + j < n) wk.S[(size_t)(p0 + i) * wk.lds + q0 + j] = Tl[i * (kTile + 1) + j];
+    if (p0 + i < n && q0 + j < n) {
+      const size_t o = (size_t)(p0 + i) * wk.lds + q0 + j;
+      float sv = Tl[i * (kTile + 1) + j];
+      if (pb.box && p0 + i != q0 + j) sv -= abox * (wk.ybp[o] - wk.ybm[o]);
+      wk.S[o] = sv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Element-wise box -u <= X_pq <= u (p != q) as a structured row class (the
+// bounds of the MIMO relaxation, Sec. 5.3): per pair p < q the rows
+// X_pq <= u and -X_pq <= u, i.e. A = +-s (E_pq + E_qp) / 2 with rhs s u
+// (s = sqrt(2) when the rows are scaled to unit Frobenius norm), so that
+// M(Z) = +-s Z_pq on them and M*(y) = s (y_up - y_lo) / 2 off the diagonal.
+// The dual step of Sec. 2.2, y_half = y + alpha M(2 X+ - X) followed by
+// y+ = y_half - alpha proj_{v <= rhs}(y_half / alpha), becomes per entry,
+// with z = (2 X^{k+1} - X^k)_pq formed from the factors of both iterates,
+//   y_up+ = max(0, y_up + alpha s (z - u)),   y_lo+ = max(0, y_lo - alpha s (z + u)).
+// The kernel also sums the rows' shares of eps_dual^2, <dy, M(dX)>, rhs^T y
+// and ||M*(dy)||_F^2 into Ctl::red_dvals[kRedBox..].  One CTA per tile pair
+// bi <= bj; it writes (p, q) and, through shared memory, (q, p).
+constexpr int BX_C = 32;  // factor columns staged per pass
+
+__global__ void __launch_bounds__(256) k_box_dual(DevProblem pb, DevWork wk, int r) {
+  __shared__ float smb[4 * kTile * (BX_C + 1)];
+  __shared__ double sh[32 * 4];
+  float* An = smb;                        // kTile x (BX_C+1): lambda_+ V rows p, new iterate
+  float* Bn = An + kTile * (BX_C + 1);    // V rows q, new iterate
+  float* Ao = Bn + kTile * (BX_C + 1);    // the same for the previous iterate
+  float* Bo = Ao + kTile * (BX_C + 1);
+  Ctl* ctl = wk.ctl;
+  const int nw = 1 - ctl->par, od = ctl->par;
+  const int ro = ctl->r_old;
+  const int T = pb.ntile;
+  int b = blockIdx.x, bi = 0;
+  while (bi < T && b >= T - bi) {  // row bi of the upper tile triangle holds T - bi tiles
+    b -= T - bi;
+    ++bi;
+  }
+  const int bj = bi + b;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int n = pb.n;
+  const int p0 = bi * kTile, q0 = bj * kTile;
+  float xn[4][4], xo[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      xn[a][c] = 0.f;
+      xo[a][c] = 0.f;
+    }
+  const int rm = max(r, ro);
+  for (int t0 = 0; t0 < rm; t0 += BX_C) {
+    for (int idx = tid; idx < kTile * BX_C; idx += blockDim.x) {
+      const int i = idx / BX_C, tt = idx % BX_C, t = t0 + tt;
+      const bool okp = p0 + i < n, okq = q0 + i < n;
+      const float ln = (t < r) ? (float)fmax(wk.lam[nw][t], 0.0) : 0.f;
+      const float lo = (t < ro) ? (float)fmax(wk.lam[od][t], 0.0) : 0.f;
+      An[i * (BX_C + 1) + tt] = (okp && t < r) ? ln * wk.Vrm[nw][(size_t)(p0 + i) * wk.ldv + t] : 0.f;
+      Bn[i * (BX_C + 1) + tt] = (okq && t < r) ? wk.Vrm[nw][(size_t)(q0 + i) * wk.ldv + t] : 0.f;
+      Ao[i * (BX_C + 1) + tt] = (okp && t < ro) ? lo * wk.Vrm[od][(size_t)(p0 + i) * wk.ldv + t] : 0.f;
+      Bo[i * (BX_C + 1) + tt] = (okq && t < ro) ? wk.Vrm[od][(size_t)(q0 + i) * wk.ldv + t] : 0.f;
+    }
+    __syncthreads();
+    const int tn = min(BX_C, rm - t0);
+    for (int t = 0; t < tn; ++t) {
+      float an[4], ao[4], bn[4], bo[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        an[a] = An[(ty + 16 * a) * (BX_C + 1) + t];
+        ao[a] = Ao[(ty + 16 * a) * (BX_C + 1) + t];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        bn[c] = Bn[(tx + 16 * c) * (BX_C + 1) + t];
+        bo[c] = Bo[(tx + 16 * c) * (BX_C + 1) + t];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          xn[a][c] = fmaf(an[a], bn[c], xn[a][c]);
+          xo[a][c] = fmaf(ao[a], bo[c], xo[a][c]);
+        }
+    }
+    __syncthreads();
+  }
+  float* Ut = smb;                        // kTile x (kTile+1): new y_up of the tile, then transposed out
+  float* Lt = smb + kTile * (kTile + 1);  // new y_lo
+  const double alpha = pb.alpha;
+  const float as = (float)(alpha * (double)pb.box_s), u = pb.box_u;
+  const double s = pb.box_s, su = (double)pb.box_s * (double)pb.box_u;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = ty + 16 * a, j = tx + 16 * c;
+      const int p = p0 + i, q = q0 + j;
+      if (p < q && q < n) {
+        const size_t o = (size_t)p * wk.lds + q;
+        const float z = 2.f * xn[a][c] - xo[a][c], dx = xn[a][c] - xo[a][c];
+        const float yu = wk.ybp[o], yl = wk.ybm[o];
+        const float yun = fmaxf(0.f, yu + as * (z - u));
+        const float yln = fmaxf(0.f, yl - as * (z + u));
+        wk.ybp[o] = yun;
+        wk.ybm[o] = yln;
+        Ut[i * (kTile + 1) + j] = yun;
+        Lt[i * (kTile + 1) + j] = yln;
+        const double du = (double)yun - (double)yu, dl = (double)yln - (double)yl;
+        const double mdx = s * (double)dx;  // M(X+ - X) on the upper row; its negative on the lower
+        const double e1 = du / alpha - mdx, e2 = dl / alpha + mdx;
+        v[0] += e1 * e1 + e2 * e2;
+        v[1] += mdx * (du - dl);
+        v[2] += su * ((double)yun + (double)yln);
+        v[3] += 0.5 * s * s * (du - dl) * (du - dl);
+      }
+    }
+  __syncthreads();
+  for (int idx = tid; idx < kTile * kTile; idx += blockDim.x) {  // (q, p): consecutive threads, consecutive p
+    const int j = idx / kTile, i = idx % kTile;
+    const int p = p0 + i, q = q0 + j;
+    if (p < q && q < n) {
+      const size_t o = (size_t)q * wk.lds + p;
+      wk.ybp[o] = Ut[i * (kTile + 1) + j];
+      wk.ybm[o] = Lt[i * (kTile + 1) + j];
+    }
+  }
+  block_sum<4>(v, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) wk.part[(size_t)blockIdx.x * 4 + k] = v[k];
+  if (!last_block(&wk.counters[CNT_BOX * 512])) return;
+  __shared__ double tot[4];
+  reduce_partials(wk.part, gridDim.x, 4, 4, tot);
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) ctl->red_dvals[kRedBox + k] = tot[k];
+    wk.counters[CNT_BOX * 512] = 0u;
   }
 }
 
@@ -747,7 +887,8 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int i
   const int per = (act + GC_T - 1) / GC_T;
   const int tiles = per * 2 * per * 2;
   int ns = 1;
-  while (ns < 8 && tiles * ns * 2 <= 148 && pb.n >= 2 * ns * 256) ns *= 2;
+  const int sms = num_sms();
+  while (ns < 8 && tiles * ns * 2 <= sms && pb.n >= 2 * ns * 256) ns *= 2;
   const int rows = (pb.n + ns - 1) / ns;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(tiles, ns, 1);
@@ -761,6 +902,11 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int i
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, k_gram_control, pb, wk, act, rows, iter_launches, cond, use_cond);
+}
+
+void launch_box_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st) {
+  const int T = pb.ntile;
+  k_box_dual<<<T * (T + 1) / 2, 256, 0, st>>>(pb, wk, r);
 }
 
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st) {

@@ -107,6 +107,11 @@ struct DevProblem {
   const int* tile_u;           // union entry index
   double alpha;
   double normC, normRhs;       // ||C||_F, ||rhs||_2 (scaled problem)
+  // element-wise box -u <= X_pq <= u for all p != q as a structured row
+  // class (duals in DevWork::ybp / ybm): rows +-box_s (E_pq + E_qp) / 2 with
+  // rhs box_s * u; box = 0 when absent
+  int box;
+  float box_s, box_u;
   const double* C_dense;       // dense C (row-major n x n) or nullptr
   // rows of the full (both triangles) union pattern, for the factored
   // operator: row i holds entries [sym_ptr[i], sym_ptr[i+1]) at columns
@@ -146,10 +151,19 @@ struct DevWork {
   float* Dsym;                 // (float)(alpha * D) on the full pattern, CSR order of sym_col
   float* Qr;                   // row-major copy of the block being multiplied (n x w)
   float* lrP;                  // its coefficient block [Lambda_+ V^T Q ; -alpha s0 1^T Q]
+  // duals of the box rows X_pq <= u (ybp) and -X_pq <= u (ybm), algorithm
+  // sign (>= 0), scaled problem: n x n symmetric, row stride lds (nullptr
+  // without a box)
+  float* ybp;
+  float* ybm;
   Ctl* ctl;
 };
 
-enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_NUM };
+enum CounterId { CNT_GRAM = 0, CNT_RITZ, CNT_DUAL, CNT_DVALS, CNT_CTL, CNT_BOX, CNT_NUM };
+
+// Ctl::red_dvals slots written by the box kernel: its rows' shares of
+// eps_dual^2, <dy, M(dX)>, rhs^T y and ||M*(dy)||_F^2
+constexpr int kRedBox = 4;
 
 // ---------------------------------------------------------------------------
 // launchers (k_lanczos.cu)
@@ -225,6 +239,11 @@ void launch_gram_control(const DevProblem& pb, const DevWork& wk, int act, int i
                          cudaGraphConditionalHandle cond, int use_cond, cudaStream_t st);
 // sel = 0: factors of the current iterate (Ctl::par); sel = 1: the other buffer.
 void launch_rebuild(const DevProblem& pb, const DevWork& wk, int r, int sel, cudaStream_t st);
+// Dual step of the element-wise box rows and their residual / objective
+// shares (after launch_dvals, before launch_gram_control).
+void launch_box_dual(const DevProblem& pb, const DevWork& wk, int r, cudaStream_t st);
+// Streaming multiprocessors of the current device (launch heuristics).
+int num_sms();
 
 // ---------------------------------------------------------------------------
 // launchers (k_factored.cu)

@@ -151,6 +151,7 @@ int Solver::upload(const HostProblem& h, bool alloc_S) {
   has_problem = false;
   has_iterate = false;
   hp = h;
+  box_u = 0.0;
   const int n = h.n;
   DevProblem& P = pb;
   P = DevProblem{};
@@ -475,14 +476,16 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   dbg(wk, "projection", st);
   launch_mxdual(pb, wk, k.r, st);
   launch_dvals(pb, wk, st);
+  if (pb.box) launch_box_dual(pb, wk, k.r, st);
   dbg(wk, "mxdual/dvals", st);
   const int act = std::min(kMaxR, ((k.r + 15) / 16) * 16);
   // kernels per iteration outside the restart cycles: Cholesky-QR, the warm
   // product, M(X)/dual step, D values, Gram + controller, the rebuild of S
-  const int iter_launches = k.full ? 7
-                                   : cholqr_kernel_count(n, k.w) +
-                                         (factored ? kFactoredLaunches + 3
-                                                   : 4 + block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
+  const int iter_launches = (k.full ? 7
+                                    : cholqr_kernel_count(n, k.w) +
+                                          (factored ? kFactoredLaunches + 3
+                                                    : 4 + block_matvec_kernels(wk.S, wk.lds, wk.mv_part))) +
+                            (pb.box ? 1 : 0);
   launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
   dbg(wk, "gram+control", st);
   if (!factored) {
@@ -543,6 +546,10 @@ int Solver::read_ctl() {
 int Solver::init_iterate_zero() {
   const int n = hp.n;
   CK(cudaMemsetAsync(wk.y, 0, sizeof(double) * std::max(hp.m, 1), st));
+  if (pb.box) {
+    CK(cudaMemsetAsync(wk.ybp, 0, sizeof(float) * (size_t)n * wk.lds, st));
+    CK(cudaMemsetAsync(wk.ybm, 0, sizeof(float) * (size_t)n * wk.lds, st));
+  }
   CK(cudaMemsetAsync(wk.dy, 0, sizeof(double) * std::max(hp.m, 1), st));
   for (int b = 0; b < 2; ++b) {
     CK(cudaMemsetAsync(wk.Vrm[b], 0, sizeof(float) * (size_t)n * kMaxR, st));
@@ -589,6 +596,48 @@ int Solver::init_iterate_zero() {
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   has_iterate = true;
+  return PROXSDP_OK;
+}
+
+// Element-wise box -u <= X_pq <= u for all p != q (Sec. 5.3) as a structured
+// class of n (n - 1) inequality rows: A = +-(E_pq + E_qp) / 2, rhs u, scaled
+// by s = sqrt(2) to unit Frobenius norm when rows are normalised.  Supported
+// when every other row acts on the diagonal only: the two parts of M*M then
+// act on orthogonal subspaces (diagonal / off-diagonal), so
+// ||M||^2 = max(||M_rows||^2, s^2), and the box part of M*(y) never meets
+// the other rows' part.
+int Solver::set_box(double u) {
+  if (!has_problem) return fail(PROXSDP_ERR_BAD_STATE, "set_box before set_problem");
+  if (!(u > 0.0) || !std::isfinite(u)) return fail(PROXSDP_ERR_INVALID_ARG, "box bound must be positive and finite");
+  if (factored) return fail(PROXSDP_ERR_UNSUPPORTED, "the element-wise box needs the explicit operator form");
+  if (!hp.dense_row.empty()) return fail(PROXSDP_ERR_UNSUPPORTED, "the element-wise box with a dense (11^T) row");
+  for (int row = 0; row < hp.m; ++row)
+    for (int c = hp.row_chunk[row]; c < hp.row_chunk[row + 1]; ++c)
+      for (int e = hp.chunk_beg[c]; e < hp.chunk_end[c]; ++e)
+        if (hp.ent_p[e] != hp.ent_q[e])
+          return fail(PROXSDP_ERR_UNSUPPORTED, "the element-wise box with rows off the diagonal (give them as rows)");
+  const int n = hp.n;
+  if (!pb.box) {
+    CKA(dalloc(*this, &wk.ybp, (size_t)n * wk.lds));
+    CKA(dalloc(*this, &wk.ybm, (size_t)n * wk.lds));
+  }
+  const double s = set.normalize_rows ? std::sqrt(2.0) : 1.0;
+  // row-only norms are kept in hp; the box adds its n (n - 1) rows
+  const double nr2 = hp.normRhs * hp.normRhs + (double)n * (double)(n - 1) * (s * u) * (s * u);
+  const double nm = std::max(hp.normM, s);
+  pb.box = 1;
+  pb.box_s = (float)s;
+  pb.box_u = (float)u;
+  pb.normRhs = std::sqrt(nr2);
+  pb.alpha = (set.alpha_frac > 0.0 ? set.alpha_frac : 0.95) / nm;
+  box_u = u;
+  box_normM = nm;
+  for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);  // they hold the problem by value
+  graphs.clear();
+  has_iterate = false;
+  CK(cudaMemsetAsync(wk.ybp, 0, sizeof(float) * (size_t)n * wk.lds, st));
+  CK(cudaMemsetAsync(wk.ybm, 0, sizeof(float) * (size_t)n * wk.lds, st));
+  CK(cudaStreamSynchronize(st));
   return PROXSDP_OK;
 }
 
@@ -726,8 +775,8 @@ int Solver::run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info
     info->matvecs = c.matvecs;
     info->lanczos_cycles = c.lz_cycles_total;
     info->lanczos_unconverged = c.lz_unconverged;
-    info->alpha = hp.alpha;
-    info->norm_M = hp.normM;
+    info->alpha = pb.alpha;  // with a box: the step of the extended operator
+    info->norm_M = pb.box ? box_normM : hp.normM;
     info->kernel_launches = c.launches;
   }
   return PROXSDP_OK;

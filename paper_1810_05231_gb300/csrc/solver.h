@@ -76,6 +76,10 @@ struct Solver {
     return code;
   }
   int upload(const HostProblem& h, bool alloc_S = true);
+  // element-wise box -u <= X_pq <= u (p != q) as a structured row class
+  int set_box(double u);
+  double box_u = 0.0;  // 0: no box
+  double box_normM = 0.0;  // ||M||_2 of the rows with the box
   int init_iterate_zero();
   int set_iterate(int r, const double* V, const double* lam, const double* y);
   int run(int64_t iters_cap, bool stop_on_converge, proxsdp_gpu_info* info);

@@ -217,10 +217,12 @@ def sensor_network(n_sensors: int, n_anchors: int, radius: float, seed: int, d: 
                                 n_ss=len(si), n_as=len(ak)))
 
 
-def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1, box: bool = False) -> SDPProblem:
+def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1, box: bool = False,
+         box_u: float = 1.0) -> SDPProblem:
     """Binary least-squares (MIMO detection) SDR of Sec. 5.3: diag(X) = 1 and,
-    with ``box``, the paper's elementwise bounds -1 <= X_ij <= 1 for i < j as
-    2 * n(n-1)/2 inequality rows (X_ij <= 1 and -X_ij <= 1; the diagonal is
+    with ``box``, the paper's elementwise bounds -u <= X_ij <= u (u = 1 there;
+    ``box_u``) for i < j as 2 * n(n-1)/2 inequality rows (X_ij <= u, for the
+    pairs in ``np.triu_indices(n, 1)`` order, then -X_ij <= u; the diagonal is
     fixed by the equality rows).  Each row holds one off-diagonal svec entry
     of value +-1/2, so tr(A X) = +-X_ij."""
     H = rng.normal(0.0, np.sqrt(1.0 / N), (N, N))
@@ -241,9 +243,9 @@ def mimo(N: int, rng: np.random.Generator, snr_noise_var: float = 0.1, box: bool
         col = np.concatenate([col, cols, cols])
         val = np.concatenate([val, np.full(k, 0.5), np.full(k, -0.5)])
         ptr = np.concatenate([ptr, ptr[-1] + np.arange(1, 2 * k + 1, dtype=np.int64)])
-        rhs = np.concatenate([rhs, np.ones(2 * k)])
+        rhs = np.concatenate([rhs, np.full(2 * k, float(box_u))])
     return SDPProblem(n=n, m_eq=n, A_rowptr=ptr, A_col=col, A_val=val, rhs=rhs,
-                      C_dense=C, meta=dict(kind="mimo", H=H, x=x, s=s, box=box))
+                      C_dense=C, meta=dict(kind="mimo", H=H, x=x, s=s, box=box, box_u=box_u))
 
 
 # ---------------------------------------------------------------------------

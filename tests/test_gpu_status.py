@@ -185,12 +185,12 @@ def test_resume_after_interruption_follows_the_same_iterates(pkg, graphs):
     slv.close()
 
 
-@pytest.mark.parametrize("kind", ["dense_path", "lanczos_path"])
-def test_resume_from_saved_pair(pkg, kind):
+def test_resume_from_saved_pair(pkg):
     """Restart Alg. 2 from its saved feasible pair (X_[r], y_[r]) of Sec. 3.2
-    on a fresh handle: the run reaches the stop test at the optimum of the
-    uninterrupted solve (objective within 1e-4, certificates at 1e-4)."""
-    inst = _complete(16) if kind == "dense_path" else si.maxcut_er(300, 0.03, 2)
+    on a fresh handle (K_16, saved at r = 1): the run reaches the stop test at
+    the optimum of the uninterrupted solve (objective within 1e-4,
+    certificates at 1e-4)."""
+    inst = _complete(16)
     slv = pkg.Solver(tol=1e-6, rank_init=1)
     slv.set_instance(inst)
     a = slv.solve()
@@ -202,10 +202,33 @@ def test_resume_from_saved_pair(pkg, kind):
     res.set_iterate(sv["V"], sv["lam"], sv["y"])
     b = res.resume()
     assert b.status == pkg.CONVERGED, b.as_dict()
-    assert b.final_rank >= a.final_rank // 2
     assert abs(b.primal_obj - a.primal_obj) <= 1e-4 * (1 + abs(a.primal_obj)), (a.primal_obj, b.primal_obj)
     got = res.get_primal_dual()
     cert = oracle.certificates(Problem.from_instance(inst), got["X"], -got["y"])
+    assert cert["primal_eq"] <= 1e-4 and cert["rel_gap"] <= 1e-4, cert
+    slv.close()
+    res.close()
+
+
+def test_resume_from_a_warm_start_on_the_block_lanczos_path(pkg):
+    """G(300, 0.03): the leading half of a converged factorisation and its y
+    as the starting iterate (set_iterate, rank r/2), then resume: Alg. 2 grows
+    the rank back and stops at the optimum of the cold solve."""
+    inst = si.maxcut_er(300, 0.03, 2)
+    slv = pkg.Solver(tol=1e-5, rank_init=2)
+    slv.set_instance(inst)
+    a = slv.solve()
+    assert a.status == pkg.CONVERGED, a.as_dict()
+    got = slv.get_primal_dual(want_X=False)
+    h = max(1, got["r"] // 2)
+    res = pkg.Solver(tol=1e-5, rank_init=2)
+    res.set_instance(inst)
+    res.set_iterate(got["V"][:, :h], got["lam"][:h], got["y"])
+    b = res.resume()
+    assert b.status == pkg.CONVERGED, b.as_dict()
+    assert abs(b.primal_obj - a.primal_obj) <= 1e-4 * (1 + abs(a.primal_obj)), (a.primal_obj, b.primal_obj)
+    fin = res.get_primal_dual()
+    cert = oracle.certificates(Problem.from_instance(inst), fin["X"], -fin["y"])
     assert cert["primal_eq"] <= 1e-4 and cert["rel_gap"] <= 1e-4, cert
     slv.close()
     res.close()
