@@ -642,7 +642,7 @@ def run_workload_solve(args):
     title, fn, rank0 = WORKLOAD_SOLVES[args.workload]
     inst = getattr(si, fn)()
     slv = pkg.Solver(tol=1e-4, rank_init=rank0, max_iter=10 ** 7, time_limit_s=args.time_limit, check_every=200,
-                     operator_form=OPERATOR_FORMS[args.operator])
+                     operator_form=OPERATOR_FORMS[args.operator], at_max_rank=1 if args.at_max_rank else 0)
     t0 = time.perf_counter()
     slv.set_instance(inst)
     info = slv.solve()
@@ -654,7 +654,7 @@ def run_workload_solve(args):
             "steps": 1, "warmup": 0, "ms_per_step": round(1000 * info.solve_seconds, 3), "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": fn, "n": inst.n, "tol": 1e-4, "rank_init": rank0, "operator": args.operator,
-                       "time_limit_s": args.time_limit},
+                       "time_limit_s": args.time_limit, "at_max_rank": "continue" if args.at_max_rank else "stop"},
             "converged": conv, "status": int(info.status), "iters": int(info.iters), "final_rank": info.final_rank,
             "iters_per_s": round(info.iters / max(info.solve_seconds, 1e-9), 2), "primal_obj": info.primal_obj,
             "rel_primal_res": info.rel_primal_res, "rel_dual_res": info.rel_dual_res, "rel_gap": info.rel_gap,
@@ -693,6 +693,8 @@ def main():
                     choices=["maxcut", "mimo-batch"] + sorted(SWEEPS) + sorted(WORKLOAD_SOLVES))
     ap.add_argument("--sizes", default="", help="comma-separated sizes for the table2 / table3 sweeps")
     ap.add_argument("--time-limit", type=float, default=60.0, help="per-instance cap of the sweeps (s)")
+    ap.add_argument("--at-max-rank", action="store_true",
+                    help="workload solves: keep iterating at the rank cap instead of stopping there")
     ap.add_argument("--operator", default="explicit", choices=sorted(OPERATOR_FORMS),
                     help="how the projection applies S^k: formed in HBM, or from the factors of X^k")
     ap.add_argument("--other-operator", default="factored", choices=sorted(OPERATOR_FORMS) + ["none"],

@@ -111,6 +111,11 @@ typedef struct {
   int operator_form;      /* PROXSDP_OP_EXPLICIT / _FACTORED / _AUTO                     [0]   */
   int64_t memory_limit_bytes; /* cap on the device memory one handle allocates; set_problem
                                  returns PROXSDP_ERR_OOM beyond it (0: no cap)        [0]   */
+  int at_max_rank;        /* when Alg. 2's rank rule asks for r > max_rank: 0 stops with
+                             PROXSDP_STALLED_AT_MAX_RANK; 1 keeps iterating at max_rank,
+                             and there the stop test accepts residuals and gap within
+                             tol without the rank test (the pair is then certified by
+                             its residuals and gap only)                             [0]   */
 } proxsdp_gpu_settings;
 
 typedef struct {

@@ -79,6 +79,7 @@ class Settings(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("operator_form", ctypes.c_int),
         ("memory_limit_bytes", ctypes.c_int64),
+        ("at_max_rank", ctypes.c_int),
     ]
 
 

@@ -369,7 +369,7 @@ int check_settings(const proxsdp_gpu_settings& s, std::string& err) {
       s.window > psdp::kMaxWindow || !(s.alpha_frac > 0.0 && s.alpha_frac < 1.0) || s.max_rank < 1 ||
       s.lanczos_max_cycles < 1 || s.lanczos_steps < 0 || s.lanczos_tol < 0.0 || s.guard < 0 ||
       s.check_every < 1 || s.precision != PROXSDP_PREC_FP32 || s.operator_form < PROXSDP_OP_EXPLICIT ||
-      s.operator_form > PROXSDP_OP_AUTO || s.memory_limit_bytes < 0) {
+      s.operator_form > PROXSDP_OP_AUTO || s.memory_limit_bytes < 0 || s.at_max_rank < 0 || s.at_max_rank > 1) {
     err = "invalid settings";
     return PROXSDP_ERR_INVALID_ARG;
   }
@@ -464,6 +464,8 @@ int proxsdp_gpu_settings_default(proxsdp_gpu_settings* s) {
   s->check_every = 50;
   s->use_graphs = 1;
   s->operator_form = PROXSDP_OP_EXPLICIT;
+  s->memory_limit_bytes = 0;
+  s->at_max_rank = 0;
   return PROXSDP_OK;
 }
 

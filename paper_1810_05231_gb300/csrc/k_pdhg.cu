@@ -473,8 +473,11 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
     const bool conv = fmax(rel_p, rel_d) <= ctl->tol;
     const bool rank_ok = (r >= n) || ctl->full_eig ||
                          (sqrt((double)(n - r)) * fmax(lam_r, 0.0) <= ctl->eps_lambda * fmax(1.0, normX));
+    // at the rank cap with settings.at_max_rank, the residuals and the gap
+    // alone decide (r cannot grow)
+    const bool cap_ok = ctl->at_max_rank && r >= ctl->max_rank;
     bool grow = false;
-    if (conv && rank_ok) {
+    if (conv && (rank_ok || cap_ok)) {
       if (rel_gap <= ctl->tol) status = ST_CONVERGED;
     } else if (conv) {
       ctl->saved += 1;  // feasible (X_[r], y_[r]) of Alg. 2
@@ -483,7 +486,7 @@ __device__ void control_tail(const DevProblem& pb, const DevWork& wk, const doub
       grow = !rank_ok;
     }
     if (grow && !ctl->fixed_rank) {
-      if (r >= ctl->max_rank || r >= n) status = ST_STALLED_MAX_RANK;
+      if (r >= ctl->max_rank || r >= n) status = ctl->at_max_rank ? ST_RUNNING : ST_STALLED_MAX_RANK;
       else status = ST_RANK_CHANGE;
     }
     if (status == ST_RUNNING && it >= ctl->it_stop) status = ST_PAUSE;

@@ -60,7 +60,7 @@ struct Ctl {
   int max_cycles;
   int fixed_rank;    // 1: never change r (building-block use)
   int full_eig_path; // projection by the dense eigensolver (n <= 128 or Alg. 1)
-  int pad1;
+  int at_max_rank;   // 1: keep iterating at max_rank instead of stopping (settings.at_max_rank)
   long long matvecs;
   long long lz_cycles_total;
   long long lz_unconverged;

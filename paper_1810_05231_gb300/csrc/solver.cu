@@ -578,6 +578,7 @@ int Solver::init_iterate_zero() {
   c.full_eig_path = (n <= kFullEigMax || set.full_eig) ? 1 : 0;
   c.window = std::max(1, std::min(set.window, kMaxWindow));
   c.max_rank = rank_cap();
+  c.at_max_rank = set.at_max_rank ? 1 : 0;
   c.max_cycles = std::max(1, set.lanczos_max_cycles);
   c.tol = set.tol;
   c.eps_lambda = set.eps_lambda > 0 ? set.eps_lambda : set.tol;

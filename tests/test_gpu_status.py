@@ -76,6 +76,28 @@ def test_status_stalled_at_max_rank(pkg, inst_kind):
     slv.close()
 
 
+@pytest.mark.parametrize("inst_kind", ["dense_path", "lanczos_path"])
+def test_at_max_rank_keeps_iterating(pkg, inst_kind):
+    """The same capped instances with settings.at_max_rank = 1: the solve
+    stays at r = 2 and runs on instead of stopping.  Where it meets the stop
+    test there (residuals and gap, the rank test waived at the cap) the pair
+    is optimal: K_16 (n even) also has rank-1 optima, X = x x^T for any
+    balanced +-1 vector x, and the value is the closed form n^2 / 4."""
+    inst = _complete(16) if inst_kind == "dense_path" else si.maxcut_er(300, 0.03, 2)
+    slv = pkg.Solver(tol=1e-6, rank_init=1, max_rank=2, max_iter=20000, at_max_rank=1)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status in (pkg.MAX_ITER, pkg.CONVERGED), info.as_dict()
+    assert info.final_rank == 2
+    if inst_kind == "dense_path":
+        assert info.status == pkg.CONVERGED, info.as_dict()
+        assert abs(info.primal_obj + 64.0) <= 1e-4 * 64.0, info.primal_obj
+    slv.close()
+    with pytest.raises(pkg.ProxSDPError) as e:
+        pkg.Solver(at_max_rank=2)
+    assert e.value.code == pkg.ERR_INVALID_ARG
+
+
 def test_status_numeric_error(pkg):
     """C entries of 1e200 are finite in FP64 (accepted by set_problem) but
     overflow FP32 in S^k: the iteration reports NUMERIC_ERROR, and the handle

@@ -101,3 +101,32 @@ def test_equipartition_5000(pkg):
     feas = np.linalg.norm(MX[: sp.m_eq] - sp.rhs[: sp.m_eq]) / (1.0 + np.linalg.norm(sp.rhs[: sp.m_eq]))
     assert feas <= 1e-2, feas
     slv.close()
+
+
+def test_equipartition_5000_to_1e4_at_the_rank_cap(pkg):
+    """n = 5000 run to the 1e-4 stop test: Alg. 2's rank rule asks for
+    r = 128 once r = 64 (the Lanczos path's cap) stalls; with
+    settings.at_max_rank = 1 the solve keeps iterating at r = 64 and meets the
+    residual and gap tests there (about 50 000 iterations).  The FP64 oracle's
+    certificates of the returned pair, computed on the host from the
+    instance, check it independently of the solver's own reductions: primal
+    feasibility, the dual slack C + M*(y) (its smallest eigenvalue) and the
+    gap."""
+    inst = si.config_equipartition_5000()
+    slv = pkg.Solver(tol=1e-4, rank_init=16, max_iter=10**6, time_limit_s=500.0, check_every=200, at_max_rank=1)
+    slv.set_instance(inst)
+    info = slv.solve()
+    assert info.status == pkg.CONVERGED, info.as_dict()
+    assert info.final_rank == 64
+    got = slv.get_primal_dual()
+    slv.close()
+    # on the row-scaled problem the iteration runs on (reading A6): the dense
+    # row 11^T has ||A_i||_F = n, so its residual in the original units is n
+    # times the scaled one
+    sp, scale = oracle.normalize_rows(Problem.from_instance(inst))
+    cert = oracle.certificates(sp, got["X"], -got["y"] / scale)
+    print("certificates", cert)
+    assert cert["primal_eq"] <= 1e-4, cert
+    assert cert["rel_gap"] <= 2e-4, cert  # the stop test's gap (reading A21)
+    assert cert["x_min_eig_rel"] >= -1e-6, cert
+    assert cert["dual_min_eig_rel"] >= -1e-4, cert
