@@ -628,8 +628,8 @@ bool block_matvec_tc_enabled() {
   return !off && encode_fn() != nullptr;
 }
 
-bool block_matvec_tc_applies(const float* S, int lds, const float* scratch) {
-  return scratch && block_matvec_tc_enabled() && !(lds & 3) && !(reinterpret_cast<uintptr_t>(S) & 15) &&
+bool block_matvec_tc_applies(const float* S, int lds, int n, const float* scratch) {
+  return scratch && n >= kTcMinN && block_matvec_tc_enabled() && !(lds & 3) && !(reinterpret_cast<uintptr_t>(S) & 15) &&
          !(reinterpret_cast<uintptr_t>(scratch) & 15);
 }
 
@@ -647,7 +647,7 @@ static int tc_slices(int n, int tiles, int sms, int per_sm) {
 bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int ldq, float* W, int ldw, int k,
                             const int* skip, cudaStream_t st, float* scratch, cudaGraphConditionalHandle cond,
                             int set_cond) {
-  if (!block_matvec_tc_applies(S, lds, scratch) || n < 1 || k < 1) return false;
+  if (!block_matvec_tc_applies(S, lds, n, scratch) || k < 1) return false;
   const int ld2 = (n + 31) / 32 * 32;
   float* Qhi = scratch;
   float* Qlo = scratch + (size_t)ld2 * k;

@@ -191,10 +191,18 @@ bool launch_block_matvec_tc(const float* S, int lds, int n, const float* Q, int 
                             const int* skip, cudaStream_t st, float* scratch, cudaGraphConditionalHandle cond,
                             int set_cond);
 size_t block_matvec_tc_scratch_floats(int n, int k);
-bool block_matvec_tc_applies(const float* S, int lds, const float* scratch);
+// The tensor-core product runs from kTcMinN up.  Below it S (<= 4 MB) stays
+// in L2, where the SIMT kernel takes the same time (measured at n = 2000:
+// 28 us each), and the SIMT product's bias is about 100x smaller (-1e-9
+// against -9e-8 relative): on MIMO relaxations at n = 284..511 that bias
+// left the duality gap at 2e-4..4e-4 with residuals near 1e-6 (45 of 256
+// instances of the batch workload), and the same instances converge with the
+// SIMT product.
+constexpr int kTcMinN = 1024;
+bool block_matvec_tc_applies(const float* S, int lds, int n, const float* scratch);
 // kernels one launch_block_matvec enqueues (the tensor-core path splits Q first)
-inline int block_matvec_kernels(const float* S, int lds, const float* scratch) {
-  return block_matvec_tc_applies(S, lds, scratch) ? 2 : 1;
+inline int block_matvec_kernels(const float* S, int lds, int n, const float* scratch) {
+  return block_matvec_tc_applies(S, lds, n, scratch) ? 2 : 1;
 }
 bool block_matvec_tc_enabled();
 void init_mv_tc_attributes();

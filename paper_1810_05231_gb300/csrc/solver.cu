@@ -399,7 +399,7 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
     launch_gram(wk.Q, wk.ldq, K, wk.W, wk.ldq, K, n, wk.H, wk.part, wk.counters + CNT_GRAM * 512, skip, st);
     launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
     const int launches = 4 + orth_kernel_count(n, w, bx, false) +
-                         (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
+                         (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, n, wk.mv_part));
     launch_ritz(wk, n, K, w, r, 1, launches, cond, use_cond, st);
     dbg(wk, "ritz", st);
     return;
@@ -417,7 +417,7 @@ void enqueue_cycle(const DevWork& wk, int n, int w, int K, int s, int r,
   launch_sym_eig(wk.H, K, wk.theta, wk.Y, kMaxK, w, skip, st, 1, &wk.ctl->lz_tol);
   dbg(wk, "rr eig", st);
   // Gram of T, eigensolver, Ritz; the products
-  int cycle_launches = 3 + s * (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, wk.mv_part));
+  int cycle_launches = 3 + s * (fac ? kFactoredLaunches : block_matvec_kernels(wk.S, wk.lds, n, wk.mv_part));
   for (int j = 1; j <= s; ++j) cycle_launches += orth_kernel_count(n, j * w, w, true);
   launch_ritz(wk, n, K, w, r, s, cycle_launches, cond, use_cond, st);
   dbg(wk, "ritz", st);
@@ -484,7 +484,7 @@ int Solver::enqueue_iteration(const GraphKey& k, bool in_graph, cudaGraphConditi
   const int iter_launches = (k.full ? 7
                                     : cholqr_kernel_count(n, k.w) +
                                           (factored ? kFactoredLaunches + 3
-                                                    : 4 + block_matvec_kernels(wk.S, wk.lds, wk.mv_part))) +
+                                                    : 4 + block_matvec_kernels(wk.S, wk.lds, n, wk.mv_part))) +
                             (pb.box ? 1 : 0);
   launch_gram_control(pb, wk, act, iter_launches, outer, use, st);
   dbg(wk, "gram+control", st);
