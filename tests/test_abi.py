@@ -53,8 +53,9 @@ def test_struct_layout_matches_c(built):
 #include <stddef.h>
 #include "proxsdp_gpu.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(proxsdp_gpu_settings), offsetof(proxsdp_gpu_settings, lanczos_tol),
-         offsetof(proxsdp_gpu_settings, use_graphs), sizeof(proxsdp_gpu_info), offsetof(proxsdp_gpu_info, norm_M));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(proxsdp_gpu_settings), offsetof(proxsdp_gpu_settings, lanczos_tol),
+         offsetof(proxsdp_gpu_settings, use_graphs), sizeof(proxsdp_gpu_info), offsetof(proxsdp_gpu_info, norm_M),
+         offsetof(proxsdp_gpu_settings, memory_limit_bytes), offsetof(proxsdp_gpu_settings, at_max_rank));
   return 0;
 }
 '''
@@ -65,13 +66,15 @@ int main(void) {
         subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     S, I = built.Settings, built.Info
-    assert vals == [ctypes.sizeof(S), S.lanczos_tol.offset, S.use_graphs.offset, ctypes.sizeof(I), I.norm_M.offset]
+    assert vals == [ctypes.sizeof(S), S.lanczos_tol.offset, S.use_graphs.offset, ctypes.sizeof(I), I.norm_M.offset,
+                    S.memory_limit_bytes.offset, S.at_max_rank.offset]
 
 
 def test_settings_defaults_without_gpu(built):
     s = built.default_settings()
     assert s.tol == 1e-4 and s.rank_init == 8 and s.block_size == 16 and s.window == 100
     assert abs(s.alpha_frac - 0.95) < 1e-15 and s.normalize_rows == 1
+    assert s.max_rank == 64 and s.at_max_rank == 0 and s.memory_limit_bytes == 0 and s.operator_form == 0
 
 
 def test_create_fails_loudly_without_gpu(built):
