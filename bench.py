@@ -552,6 +552,12 @@ def run_mimo_batch(args):
     return 0
 
 
+def main_config(args, world):
+    """The workload of the main line, printed identically by both arms."""
+    return {"workload": WORKLOAD, "n": 2000, "rank_init": 8, "block": 16, "tol": 1e-4, "operator": args.operator,
+            "l2": "flushed before each timed solve", "parallelism": "replicas" if world > 1 else "single"}
+
+
 def mimo_batch_leg(n_inst, host_threads):
     """Config 5 beside the main line: n_inst MIMO relaxations (N log-uniform in
     [32, 512], seed 4) solved to 1e-4 through proxsdp_gpu_solve_batch (one
@@ -772,7 +778,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1000 * total_t / max(args.steps, 1), 3), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "rank": 8, "tol": 1e-4},
+                "config": main_config(args, 1),
                 "cpu_baseline": {"value": round(value, 4), "unit": "iters/s", "cores": os.cpu_count(),
                                  "kind": "oracle", "sample": f"{total_k} LR-PD-SDP iterations (exact eigh) of the n=2000 workload"},
                 "e2e": {"value": round(value, 4), "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -816,8 +822,7 @@ def main():
         "metric": METRIC, "value": round(value, 2), "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * total_t / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": 2000, "rank_init": 8, "block": 16, "tol": 1e-4, "operator": args.operator,
-                   "l2": "flushed before each timed solve", "parallelism": "replicas" if world > 1 else "single"},
+        "config": main_config(args, world),
         "time_to_tol_s": round(statistics.median(res["times"]), 5),
         "iters_per_solve": int(statistics.median(res["iters"])),
         "final_rank": info["final_rank"], "primal_obj": info["primal_obj"], "rel_gap": info["rel_gap"],
