@@ -305,8 +305,7 @@ int proxsdp_gpu_aproj(const float* S, int64_t n, int64_t lds, int r, float* P, i
  * Limits: n <= 2048 (larger n returns PROXSDP_ERR_UNSUPPORTED with a message
  * for proxsdp_gpu_last_error(NULL)); r as for proxsdp_gpu_aproj.
  * The first call on a device looks up the array's device address on that
- * device with cudaGetSymbolAddress and keeps it for later calls; make that
- * first call before any stream capture on the device.  The kept address
+ * device with cudaGetSymbolAddress and keeps it for later calls.  The kept address
  * belongs to the device's primary context: after cudaDeviceReset (or any
  * other end of that context) the process must not call this entry point
  * again on that device.  All calls share the one array, which keeps the
