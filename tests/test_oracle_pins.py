@@ -249,6 +249,19 @@ def test_maxcut_cycle_closed_form(n, mode):
     assert abs(res.pobj - want) < 1e-5 * abs(want)
 
 
+@pytest.mark.parametrize("n,mode", [(64, "lr"), (101, "full")])
+def test_maxcut_cycle_closed_form_larger(n, mode):
+    """The cycle closed forms at n = 64 (even: n) and n = 101 (odd:
+    (n/2)(1 + cos(pi/n))), tolerance 1e-6: Alg. 2 on the 64-cycle (about
+    2 000 iterations), Alg. 1 on the 101-cycle (about 28 000 iterations,
+    half a minute; PDHG approaches the odd-cycle optimum slowly)."""
+    prob = Problem.from_instance(si.maxcut(n, *si.cycle_graph(n)))
+    res = oracle.solve(prob, mode=mode, tol=1e-6, rank_init=1, max_iter=100000)
+    want = -(n / 2.0) * (1.0 + math.cos(math.pi / n)) if n % 2 else -float(n)
+    assert res.status == 0
+    assert abs(res.pobj - want) < 1e-5 * abs(want)
+
+
 @pytest.mark.parametrize("n", [6, 8])
 def test_equipartition_closed_forms(n):
     ei, ej, w = si.complete_graph(n)
