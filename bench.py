@@ -271,15 +271,17 @@ def block_product_roofline(pkg, torch, stream, n, k, launches=10, reps=5):
     torch.cuda.empty_cache()
     t = statistics.mean(durs)
     bytes_alg = n * n * 4 + 2 * n * k * 4
+    # the library runs the tensor-core kernel from n = 1024 up (kTcMinN), the SIMT one below
+    kernel = "k_block_matvec_tc" if n >= 1024 else "k_block_matvec"
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get(f"k_block_matvec_n{n}_k{k}")
+            traffic = json.load(open(tp)).get(f"{kernel}_n{n}_k{k}")
         except Exception:
             traffic = None
     achieved = bytes_alg / t / 1e9
-    return {"kernel": "k_block_matvec", "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
+    return {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
             "peak_source": src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic,
             "n": n, "k": k, "alg_bytes_per_launch": bytes_alg, "avg_launch_s": t, "launches_timed": len(durs),
             "flops_per_launch": 2.0 * n * n * k, "tflops": round(2.0 * n * n * k / t / 1e12, 2),
